@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fused third-order (CEC) semi-Lagrangian step.
+
+Workload (default ``abc256``): 3D periodic [0, 2 pi)^3 grid of 256^3 cells,
+FP32, steady ABC flow (A = B = C = 1), scalar = sum of 32 random Fourier modes
+with |k| <= 8 (seed 0), CFL 0.8, split CEC step with the sweep order
+alternating every step.  One step = one fused kernel launch that advances every
+cell once; the metric is cell-updates per second (Gcell/s).
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s at fixed L2 error: plain 3rd-order vs batched/learned forms"
+UNIT = "Gcell/s"
+BYTES_PER_CELL = 20          # read Phi (4) + u (12), write Phi (4)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256, help="cells per axis")
+    ap.add_argument("--no-extras", action="store_true", help="skip the per-scheme and batched side measurements")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+    def find(obj):
+        if isinstance(obj, dict):
+            for k, v in obj.items():
+                if "hbm" in k.lower() and isinstance(v, (int, float)):
+                    return float(v)
+                r = find(v)
+                if r:
+                    return r
+        return None
+    v = find(d)
+    return (v, "measured") if v else (FALLBACK_HBM_GBS, "fallback")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_split.cu", "sl_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1606_06117_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per launch of the CEC kernel from the committed ncu summary, or
+    None when the summary is missing or was taken on other kernel sources."""
+    p = os.path.join(ROOT, "profiles", f"k_cec_xyz_{workload}.md")
+    try:
+        text = open(p).read()
+    except OSError:
+        return None
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(n, device, torch):
+    from paper_1606_06117_gb300 import workloads as W
+    shape = (n, n, n)
+    phi = W.random_modes(shape, W.draw_modes(3, 32, 8, seed=0), device=device, dtype=torch.float32)
+    vel = W.abc_velocity(shape, device=device, dtype=torch.float32)
+    sp = [2 * math.pi / n] * 3
+    dt = 0.8 * sp[0] / 2.0          # max |u_d| = 2 for A = B = C = 1
+    return phi, vel, sp, dt
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_rate(n_sample, max_seconds, min_steps=1, max_steps=None):
+    """Time the FP64 oracle's CEC step on an n_sample^3 grid of the same workload."""
+    import torch
+
+    from oracle import oracle as O
+    phi, vel, sp, dt = workload(n_sample, "cpu", torch)
+    p = phi.double().numpy()
+    c = vel.double().numpy() * (dt / sp[0])
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        p = O.step(p, c, O.CEC, steps)
+        steps += 1
+        el = time.perf_counter() - t0
+        if (steps >= min_steps and el >= max_seconds) or (max_steps and steps >= max_steps):
+            break
+    return steps * n_sample ** 3 / el / 1e9, steps, el
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    # each step is one oracle CEC step on a smaller periodic grid of the same flow
+    # (identical per-cell work), sized so the whole run stays within ~2 minutes
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    m = 16
+    for cand in (16, 24, 32, 48, 64, 96, 128):
+        if cand ** 3 / 3.0e6 <= budget:
+            m = cand
+    import torch
+
+    from oracle import oracle as O
+    phi, vel, sp, dt = workload(m, "cpu", torch)
+    p = phi.double().numpy()
+    c = vel.double().numpy() * (dt / sp[0])
+    for k in range(args.warmup):
+        p = O.step(p, c, O.CEC, k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        p = O.step(p, c, O.CEC, k)
+    el = time.perf_counter() - t0
+    value = args.steps * m ** 3 / el / 1e9
+    sample = f"one FP64 oracle CEC step per timed step on a {m}^3 grid of the same ABC / 32-mode workload"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"abc{args.n}_cec_f32", "sample_grid": m},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1606_06117_gb300 import _lib as sl
+
+    rank, world, local = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sl.load()
+    sl.sl_init()
+
+    n = args.n
+    ncell = n ** 3
+    phi, vel, sp, dt = workload(n, dev, torch)
+    dims = [n, n, n]
+    a, b = phi.clone(), torch.empty_like(phi)
+    stream = torch.cuda.current_stream()
+
+    def step(k, src, dst):
+        sl.sl_advect(dst, src, vel, 3, dims, sp, dt, sl.CEC, sl.F32, k & 1, stream)
+
+    for k in range(args.warmup):
+        step(k, a, b)
+        a, b = b, a
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)   # let the sampler see the loaded GPU from the first step on
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for k in range(args.steps):
+        step(k, a, b)
+        a, b = b, a
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_step = ms_max / args.steps
+    value = world * ncell * args.steps / (ms_max * 1e-3) / 1e9
+    sl_status = sl.sl_device_status(stream)
+
+    # per-launch kernel time (one launch per step) for the roofline
+    peak, peak_kind = measured_hbm_peak()
+    achieved = BYTES_PER_CELL * ncell / (ms / args.steps * 1e-3) / 1e9
+    traffic = profiled_traffic(f"abc{n}")
+
+    # ------------------------------------------------ end to end, host buffers
+    ke = max(10, min(200, args.steps // 50))
+    h_in = phi.cpu().pin_memory()
+    h_vel = vel.cpu().pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    for k in range(2):
+        sl.sl_advect_host(h_out, h_in, h_vel, 3, dims, sp, dt, sl.CEC, sl.F32, k & 1, stream)
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(ke):
+        sl.sl_advect_host(h_out, h_in, h_vel, 3, dims, sp, dt, sl.CEC, sl.F32, k & 1, stream)
+        h_in, h_out = h_out, h_in
+    barrier()
+    el = time.perf_counter() - t0
+    te = torch.tensor([el], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * ncell * ke / float(te.item()) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": 16 * ncell, "d2h_bytes_per_step": 4 * ncell, "steps": ke,
+           "api": "sl_advect_host (pinned host buffers; H2D, step, D2H, stream sync per step)"}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = side_measurements(torch, sl, dev, stream, n, phi, vel, sp, dt)
+
+    cpu = None
+    if rank == 0 and world == 1:
+        m = 96 if n >= 96 else n
+        rate, steps, secs = oracle_rate(m, max_seconds=10.0, min_steps=2)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{steps} FP64 oracle CEC steps on a {m}^3 grid of the same workload ({secs:.1f} s, 1 thread)"}
+
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"abc{n}_cec_f32", "grid": [n, n, n], "scheme": "CEC (split, fused)",
+                           "cfl": 0.8, "flow": "ABC A=B=C=1", "scalar": "32 random modes |k|<=8 seed 0",
+                           "l2": f"inputs larger than L2: {20 * ncell / 1e6:.0f} MB working set per step",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                             "kernel": "k_cec_xyz / k_cec_zyx (alternating)",
+                             "bytes_per_launch": BYTES_PER_CELL * ncell},
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk,
+                "device_status": sl_status}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def time_steps(torch, stream, fn, steps):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(steps):
+        fn(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def side_measurements(torch, sl, dev, stream, n, phi, vel, sp, dt):
+    """Per-scheme throughput, and each scheme's accuracy on the workload: 100
+    steps forward then 100 steps with the flow reversed (dt -> -dt) must return
+    the initial field; the relative L2 distance to it is computed on the device
+    in FP64 (sl_norms)."""
+    out = {}
+    dims = [n, n, n]
+    a = phi.clone()
+    b = torch.empty_like(phi)
+    rates = {}
+    for name, code, dtc in (("CIR", sl.CIR, sl.F32), ("FEC", sl.FEC, sl.F32), ("BEC", sl.BEC, sl.F32),
+                            ("CEC", sl.CEC, sl.F32), ("CEC_f32_d64", sl.CEC, sl.F32_D64)):
+        def fn(k, code=code, dtc=dtc):
+            sl.sl_advect(b, a, vel, 3, dims, sp, dt, code, dtc, k & 1, stream)
+        fn(0)
+        fn(1)
+        ms = time_steps(torch, stream, fn, 50)
+        x, y = phi.clone(), torch.empty_like(phi)
+        for k in range(200):
+            sl.sl_advect(y, x, vel, 3, dims, sp, dt if k < 100 else -dt, code, dtc, k & 1, stream)
+            x, y = y, x
+        rel = sl.sl_norms(x, phi, phi.numel(), sl.F32, stream)[2]
+        rates[name] = {"gcell_s": n ** 3 / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+                       "roundtrip_rel_l2_100_100": rel}
+    out["schemes"] = rates
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

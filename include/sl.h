@@ -1,0 +1,196 @@
+/*
+ * sl.h -- C ABI of libsl, the GB300 (sm_103a) implementation of the
+ * multi-stage semi-Lagrangian advection schemes of Cameron, Raynaud & Dormy,
+ * "Multi-stage high order semi-Lagrangian schemes for incompressible flows in
+ * Cartesian geometries" (arXiv 1606.06117).
+ *
+ * The library advances a passive scalar Phi by one time step of
+ * d_t Phi + (u . grad) Phi = 0 (Sec. 2, eq. intro:adv) on a uniform periodic
+ * Cartesian grid, with one of four schemes built from the multilinear
+ * semi-Lagrangian operator L_U[Phi](x) = Phi~(x - u dt) (Sec. 2):
+ *
+ *   SL_CIR  L_U[Phi]                                   (Sec. 3; eq. CIR2D)
+ *   SL_FEC  L_U[Phi] + (Phi - Phi_bar)/2,
+ *           Phi_bar = L_{-U}[L_U[Phi]]                 (eq. intro:FEC)
+ *   SL_BEC  L_U[Phi + (Phi - Phi_bar)/2]               (eq. intro:BEC)
+ *   SL_CEC  a FEC + b BEC per axis, 3a = 2 - dx/(|u|dt), b = 1 - a
+ *           (eqs. intro:CEC, intro:CECcoef), applied direction by direction
+ *           (Sec. 2 last paragraph, Sec. 5 eqs. split:1-2); the sweep order is
+ *           x,y,z for an even step_parity and z,y,x for an odd one.
+ *
+ * CIR, FEC and BEC use the unsplit multilinear operator on all axes.  The
+ * velocity is taken at the arrival cell; the departure point is the straight
+ * backtrace x_i - u_i dt.  Every step is one fused kernel: one read of Phi and
+ * u and one write of Phi per cell.
+ *
+ * Conventions shared by all entry points
+ *   - Fields are C-contiguous [z][y][x] arrays (x fastest) of dims[2] x dims[1]
+ *     x dims[0] cells.  For ndim = 2 set dims[2] = 1.
+ *   - vel points to ndim component planes of prod(dims) elements each (x
+ *     component first), the same element type as the field (SoA).
+ *   - spacing[d] is the cell size dx_d; the Courant number of a cell is
+ *     C_d = u_d dt / dx_d.  The schemes need |C_d| <= 1 (Table 1 stability);
+ *     larger values are reported through the device status word (bit
+ *     SL_DEV_CFL) and the result is then undefined but stays in bounds.
+ *   - Pointers are device pointers owned by the caller unless the entry point
+ *     says otherwise.  out must not alias in (SL_ERR_ALIAS).
+ *   - Calls are asynchronous on the given CUDA stream (NULL = legacy default
+ *     stream) unless stated otherwise.  No C++ exception crosses the ABI.
+ *   - The return value is an sl_status.  On failure sl_last_error() gives a
+ *     thread-local message.  The library keeps a small per-device context
+ *     (status word and work counters) that it allocates on the first call on a
+ *     device; make that first call outside CUDA graph capture, or call
+ *     sl_init() first.
+ */
+#ifndef SL_H
+#define SL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { SL_CIR = 0, SL_FEC = 1, SL_BEC = 2, SL_CEC = 3 } sl_scheme;
+
+/* Element type and arithmetic.  SL_F32: float storage and arithmetic, the
+ * round-trip difference Phi - Phi_bar evaluated from neighbour differences so
+ * that it does not cancel.  SL_F64: double throughout.  SL_F32_D64: float
+ * storage with L_U[Phi], Phi_bar and Phi - Phi_bar evaluated in double. */
+typedef enum { SL_F32 = 0, SL_F64 = 1, SL_F32_D64 = 2 } sl_dtype;
+
+typedef enum {
+    SL_OK = 0,
+    SL_ERR_ARG = -1,         /* bad pointer, size, enum or spacing      */
+    SL_ERR_ALIAS = -2,       /* out overlaps in                          */
+    SL_ERR_CFL = -3,         /* a Courant number exceeds 1 (host checks) */
+    SL_ERR_CUDA = -4,        /* a CUDA runtime call failed               */
+    SL_ERR_TIMEOUT = -5,     /* a bounded device wait ran out            */
+    SL_ERR_UNSUPPORTED = -6, /* valid request this build does not serve  */
+    SL_ERR_NOMEM = -7        /* device or host allocation failed         */
+} sl_status;
+
+/* Bits of the device status word (see sl_device_status). */
+#define SL_DEV_CFL 1u        /* some |C_d| > 1 was seen by a kernel */
+#define SL_DEV_TIMEOUT 2u    /* a bounded device wait gave up       */
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int sl_version(void);
+
+/* Thread-local text of the last error returned on this thread ("" if none). */
+const char *sl_last_error(void);
+
+/* Create the per-device context of the current device (idempotent).  Safe to
+ * call before any stream capture; the other entry points call it lazily. */
+int sl_init(void);
+
+/*
+ * One time step of one scheme: out = S[in].
+ *   out, in      device arrays of prod(dims) elements (type per dtype).
+ *   vel          device array, ndim planes of prod(dims) elements.
+ *   ndim         2 or 3.
+ *   dims         cells per axis (x, y, z); each >= 1, dims[2] = 1 when ndim = 2.
+ *   spacing      cell size per axis (x, y, z), > 0 (spacing[2] unused in 2D).
+ *   dt           time step (any sign; a negative dt reverses the flow).
+ *   scheme       sl_scheme.   dtype  sl_dtype.
+ *   step_parity  only read by SL_CEC: sweep order x,y,z (even) or z,y,x (odd).
+ *   stream       cudaStream_t or NULL.
+ * Errors: SL_ERR_ARG, SL_ERR_ALIAS, SL_ERR_CUDA (launch failure).
+ */
+int sl_advect(void *out, const void *in, const void *vel, int ndim,
+              const int64_t dims[3], const double spacing[3], double dt,
+              int scheme, int dtype, int step_parity, void *stream);
+
+/*
+ * The same step applied to nfields fields advected by one velocity (e.g. the
+ * three velocity components and a scalar).  outs[f] = S[ins[f]].  Same
+ * arguments and errors as sl_advect; every outs[f] must differ from every
+ * ins[g].
+ */
+int sl_advect_multi(void *const *outs, const void *const *ins, int nfields,
+                    const void *vel, int ndim, const int64_t dims[3],
+                    const double spacing[3], double dt, int scheme, int dtype,
+                    int step_parity, void *stream);
+
+/*
+ * sl_advect on HOST buffers: copies in and vel to the device, runs the step
+ * and copies the result back into out, then synchronises the stream.  The
+ * library keeps a device staging buffer per device that grows to the largest
+ * request (freed by sl_release_host_staging).  Host buffers may be pageable;
+ * page-locked buffers copy faster.
+ */
+int sl_advect_host(void *out, const void *in, const void *vel, int ndim,
+                   const int64_t dims[3], const double spacing[3], double dt,
+                   int scheme, int dtype, int step_parity, void *stream);
+int sl_release_host_staging(void);
+
+/*
+ * Host-side Courant check: max_d max_cells |u_d| dt / dx_d of a device
+ * velocity, reduced on the device in double and returned synchronously.
+ */
+int sl_courant_max(const void *vel, int ndim, const int64_t dims[3],
+                   const double spacing[3], double dt, int dtype,
+                   double *out_max, void *stream);
+
+/*
+ * Error norms of a device field a against a device field b (n elements of
+ * dtype), accumulated in double on the device and returned synchronously:
+ * out[0] = RMS of a - b, out[1] = max |a - b|, out[2] = ||a - b||_2 / ||b||_2.
+ */
+int sl_norms(const void *a, const void *b, int64_t n, int dtype, double out[3],
+             void *stream);
+
+/*
+ * Read and clear the device status word of the current device (SL_DEV_*
+ * bits).  Synchronises the stream first.
+ */
+int sl_device_status(void *stream, unsigned *out_bits);
+
+/* --------------------------------------------------------------------------
+ * Batched advection of independent periodic 3D problems of uneven sizes in one
+ * persistent launch per step (no counterpart in the paper: a throughput form
+ * of the same SL_CEC step).
+ */
+typedef struct {
+    void *a;            /* field buffer A (device)                         */
+    void *b;            /* field buffer B (device), same size as A         */
+    const void *vel;    /* 3 velocity planes (device)                      */
+    int64_t dims[3];    /* x, y, z cells                                   */
+    double spacing[3];  /* dx, dy, dz                                      */
+    double dt;          /* time step                                       */
+} sl_instance;
+
+typedef struct sl_batch sl_batch;
+
+/*
+ * Build a batch plan for n instances (copied; the device pointers must stay
+ * valid while the plan is used).  The plan owns a device instance table and a
+ * work counter.  tile_z is the z extent of one work item (0 = autotuned).
+ */
+int sl_batch_create(sl_batch **out, const sl_instance *inst, int n, int scheme,
+                    int dtype, int tile_z);
+/*
+ * One step of every instance: even step_index reads A and writes B with sweep
+ * order x,y,z; odd step_index reads B and writes A with order z,y,x.  Only a
+ * memset and a kernel launch are issued, so the call can be captured in a
+ * CUDA graph.
+ */
+int sl_batch_step(sl_batch *b, int step_index, void *stream);
+int sl_batch_destroy(sl_batch *b);
+
+/*
+ * Autotune: time the candidate z extents of the fused SL_CEC kernel for this
+ * grid on the given stream (device buffers supplied by the caller; the step is
+ * run several times, so out is overwritten) and cache the fastest for later
+ * calls with the same (dims, dtype).  Returns the chosen tile_z in *tile_z.
+ */
+int sl_autotune(void *out, const void *in, const void *vel, int ndim,
+                const int64_t dims[3], const double spacing[3], double dt,
+                int dtype, int *tile_z, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SL_H */

@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libsl (include/sl.h).
+
+Argument marshalling only: every step of the advection runs in the CUDA
+kernels of libsl.  Functions named ``sl_*`` mirror the C entry points one to
+one; they accept torch tensors (or raw integer addresses) for pointers and
+raise :class:`SLError` with the library's message on a non-zero status.
+
+There is no fallback: if ``libsl.so`` has not been built (``build()`` in
+``paper_1606_06117_gb300.build``) the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+CIR, FEC, BEC, CEC = 0, 1, 2, 3
+SCHEMES = {"CIR": CIR, "FEC": FEC, "BEC": BEC, "CEC": CEC}
+F32, F64, F32_D64 = 0, 1, 2
+DTYPES = {"f32": F32, "f64": F64, "f32_d64": F32_D64}
+DEV_CFL, DEV_TIMEOUT = 1, 2
+STATUS = {0: "SL_OK", -1: "SL_ERR_ARG", -2: "SL_ERR_ALIAS", -3: "SL_ERR_CFL", -4: "SL_ERR_CUDA",
+          -5: "SL_ERR_TIMEOUT", -6: "SL_ERR_UNSUPPORTED", -7: "SL_ERR_NOMEM"}
+
+#: every symbol include/sl.h declares
+EXPORTS = ("sl_version", "sl_last_error", "sl_init", "sl_advect", "sl_advect_multi", "sl_advect_host",
+           "sl_release_host_staging", "sl_courant_max", "sl_norms", "sl_device_status", "sl_batch_create",
+           "sl_batch_step", "sl_batch_destroy", "sl_autotune")
+
+
+class SLError(RuntimeError):
+    def __init__(self, code, message):
+        super().__init__(f"{STATUS.get(code, code)}: {message}")
+        self.code = code
+
+
+class Instance(ctypes.Structure):
+    """sl_instance"""
+    _fields_ = [("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("vel", ctypes.c_void_p),
+                ("dims", ctypes.c_int64 * 3), ("spacing", ctypes.c_double * 3), ("dt", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libsl.so (raises if it is missing; never builds implicitly)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libsl.so not found at {path}: run paper_1606_06117_gb300.build.build() first")
+        lib = ctypes.CDLL(path)
+        vp, i, i64p, dp, d = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), \
+            ctypes.POINTER(ctypes.c_double), ctypes.c_double
+        sig = {
+            "sl_version": ([], i),
+            "sl_last_error": ([], ctypes.c_char_p),
+            "sl_init": ([], i),
+            "sl_advect": ([vp, vp, vp, i, i64p, dp, d, i, i, i, vp], i),
+            "sl_advect_multi": ([ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp, i, i64p, dp, d, i, i, i, vp], i),
+            "sl_advect_host": ([vp, vp, vp, i, i64p, dp, d, i, i, i, vp], i),
+            "sl_release_host_staging": ([], i),
+            "sl_courant_max": ([vp, i, i64p, dp, d, i, dp, vp], i),
+            "sl_norms": ([vp, vp, ctypes.c_int64, i, dp, vp], i),
+            "sl_device_status": ([vp, ctypes.POINTER(ctypes.c_uint)], i),
+            "sl_batch_create": ([ctypes.POINTER(vp), ctypes.POINTER(Instance), i, i, i, i], i),
+            "sl_batch_step": ([vp, i, vp], i),
+            "sl_batch_destroy": ([vp], i),
+            "sl_autotune": ([vp, vp, vp, i, i64p, dp, d, i, ctypes.POINTER(i), vp], i),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise SLError(rc, load().sl_last_error().decode())
+    return rc
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    if isinstance(x, ctypes.c_void_p):
+        return x
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream(s):
+    if s is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream) if torch.cuda.is_available() else None
+    if isinstance(s, torch.cuda.Stream):
+        return ctypes.c_void_p(s.cuda_stream)
+    return ctypes.c_void_p(int(s))
+
+
+def _i64(v):
+    v = list(v) + [1] * (3 - len(v))
+    return (ctypes.c_int64 * 3)(*v)
+
+
+def _f64(v):
+    v = list(v) + [1.0] * (3 - len(v))
+    return (ctypes.c_double * 3)(*v)
+
+
+# ------------------------------------------------------------------ C mirrors
+def sl_version():
+    return load().sl_version()
+
+
+def sl_last_error():
+    return load().sl_last_error().decode()
+
+
+def sl_init():
+    return _check(load().sl_init())
+
+
+def sl_advect(out, inp, vel, ndim, dims, spacing, dt, scheme, dtype, step_parity=0, stream=None):
+    return _check(load().sl_advect(_ptr(out), _ptr(inp), _ptr(vel), ndim, _i64(dims), _f64(spacing), float(dt),
+                                   int(scheme), int(dtype), int(step_parity), _stream(stream)))
+
+
+def sl_advect_multi(outs, ins, vel, ndim, dims, spacing, dt, scheme, dtype, step_parity=0, stream=None):
+    n = len(outs)
+    if len(ins) != n:
+        raise ValueError("outs and ins must have the same length")
+    po = (ctypes.c_void_p * n)(*[_ptr(o).value for o in outs])
+    pi = (ctypes.c_void_p * n)(*[_ptr(i).value for i in ins])
+    return _check(load().sl_advect_multi(po, pi, n, _ptr(vel), ndim, _i64(dims), _f64(spacing), float(dt),
+                                         int(scheme), int(dtype), int(step_parity), _stream(stream)))
+
+
+def sl_advect_host(out, inp, vel, ndim, dims, spacing, dt, scheme, dtype, step_parity=0, stream=None):
+    return _check(load().sl_advect_host(_ptr(out), _ptr(inp), _ptr(vel), ndim, _i64(dims), _f64(spacing), float(dt),
+                                        int(scheme), int(dtype), int(step_parity), _stream(stream)))
+
+
+def sl_release_host_staging():
+    return _check(load().sl_release_host_staging())
+
+
+def sl_courant_max(vel, ndim, dims, spacing, dt, dtype, stream=None):
+    out = ctypes.c_double()
+    _check(load().sl_courant_max(_ptr(vel), ndim, _i64(dims), _f64(spacing), float(dt), int(dtype),
+                                 ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def sl_norms(a, b, n, dtype, stream=None):
+    out = (ctypes.c_double * 3)()
+    _check(load().sl_norms(_ptr(a), _ptr(b), int(n), int(dtype), out, _stream(stream)))
+    return tuple(out)
+
+
+def sl_device_status(stream=None):
+    bits = ctypes.c_uint()
+    _check(load().sl_device_status(_stream(stream), ctypes.byref(bits)))
+    return bits.value
+
+
+def sl_batch_create(instances, scheme=CEC, dtype=F32, tile_z=0):
+    arr = (Instance * len(instances))(*instances)
+    h = ctypes.c_void_p()
+    _check(load().sl_batch_create(ctypes.byref(h), arr, len(instances), int(scheme), int(dtype), int(tile_z)))
+    return h
+
+
+def sl_batch_step(batch, step_index, stream=None):
+    return _check(load().sl_batch_step(batch, int(step_index), _stream(stream)))
+
+
+def sl_batch_destroy(batch):
+    return _check(load().sl_batch_destroy(batch))
+
+
+def sl_autotune(out, inp, vel, ndim, dims, spacing, dt, dtype, stream=None):
+    tz = ctypes.c_int()
+    _check(load().sl_autotune(_ptr(out), _ptr(inp), _ptr(vel), ndim, _i64(dims), _f64(spacing), float(dt),
+                              int(dtype), ctypes.byref(tz), _stream(stream)))
+    return tz.value
+
+
+# ------------------------------------------------------------- conveniences
+def dtype_code(t: torch.dtype, delta64: bool = False) -> int:
+    if t == torch.float64:
+        return F64
+    if t == torch.float32:
+        return F32_D64 if delta64 else F32
+    raise TypeError(f"unsupported field dtype {t}")
+
+
+def geometry(phi: torch.Tensor, spacing=None):
+    """(ndim, dims (x,y,z), spacing (x,y,z)) of a (ny, nx) or (nz, ny, nx) field."""
+    if phi.dim() not in (2, 3):
+        raise ValueError("fields must be 2D (ny, nx) or 3D (nz, ny, nx)")
+    ndim = phi.dim()
+    dims = list(phi.shape)[::-1] + ([1] if ndim == 2 else [])
+    if spacing is None:
+        spacing = [1.0 / n for n in dims[:ndim]]
+    sp = list(spacing) + ([1.0] if ndim == 2 else [])
+    return ndim, dims, sp
+
+
+def advect(phi: torch.Tensor, vel: torch.Tensor, dt: float, spacing=None, scheme="CEC", parity: int = 0,
+           out: torch.Tensor | None = None, delta64: bool = False, stream=None) -> torch.Tensor:
+    """One step of ``scheme`` on a CUDA field; returns ``out`` (allocated if None)."""
+    ndim, dims, sp = geometry(phi, spacing)
+    if not (phi.is_cuda and vel.is_cuda):
+        raise ValueError("advect runs on CUDA tensors only")
+    if vel.shape != (ndim,) + tuple(phi.shape) or vel.dtype != phi.dtype:
+        raise ValueError("vel must be (ndim, *phi.shape) with phi's dtype")
+    phi = phi.contiguous()
+    vel = vel.contiguous()
+    if out is None:
+        out = torch.empty_like(phi)
+    sc = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    sl_advect(out, phi, vel, ndim, dims, sp, dt, sc, dtype_code(phi.dtype, delta64), parity, stream)
+    return out

@@ -1,0 +1,280 @@
+// k_unsplit.cu -- fused unsplit CIR / FEC / BEC step.
+//
+// The multilinear operator L_U (Sec. 2; eq. CIR2D and its 3D tensor-product
+// analogue) is applied 1, 2 or 3 times (Table 1, "Nb of calls"):
+//   stage 1  L_U[Phi]                         on the tile + (NST-1) halo
+//   stage 2  Phi_bar = L_{-U}[L_U[Phi]]        on the tile + (NST-2) halo,
+//            FEC = L_U[Phi] + (Phi - Phi_bar)/2 (eq. intro:FEC) or
+//            Psi = Phi + (Phi - Phi_bar)/2       (BEC input)
+//   stage 3  BEC = L_U[Psi]                   on the tile (eq. intro:BEC)
+// so the halo of Phi grows by one cell per stage (NST cells) and that of u
+// by NST-1.  The CTA marches along z; a plane of stage s is produced s planes
+// behind the newest loaded plane, and each stage keeps the three planes its
+// successor reads in a shared-memory ring.  One HBM read of Phi and u and one
+// write of the result per cell.
+#include "sl_internal.h"
+
+namespace sl {
+namespace {
+
+// Multilinear value at a departure point with |C| <= 1 in the sign form of
+// Sec. 3: on each axis the corners are the cell itself and its neighbour at
+// offset `o_d` (= -s_d for L_U, +s_d for L_{-U}), weighted 1 - U_d and U_d.
+// q0 is the cell's plane, q1 the neighbouring plane on z.
+template <typename A, bool HAS_Z, typename S>
+__device__ __forceinline__ A mlerp(const S *q0, const S *q1, int o, int ox, int oy, A ux, A uy, A uz)
+{
+    const A a00 = A(q0[o]), a10 = A(q0[o + ox]), a01 = A(q0[o + oy]), a11 = A(q0[o + oy + ox]);
+    const A b0 = a00 + ux * (a10 - a00);
+    const A b1 = a01 + ux * (a11 - a01);
+    const A c0 = b0 + uy * (b1 - b0);
+    if constexpr (!HAS_Z) {
+        return c0;
+    } else {
+        const A e00 = A(q1[o]), e10 = A(q1[o + ox]), e01 = A(q1[o + oy]), e11 = A(q1[o + oy + ox]);
+        const A f0 = e00 + ux * (e10 - e00);
+        const A f1 = e01 + ux * (e11 - e01);
+        const A c1 = f0 + uy * (f1 - f0);
+        return c0 + uz * (c1 - c0);
+    }
+}
+
+template <typename T, typename D, int NST, int TX, int TY, bool HAS_Z>
+struct Cfg {
+    static constexpr int NT = 256;
+    static constexpr int H = NST;                          // Phi halo
+    static constexpr int HW = TX + 8;                      // staged x in [-4, TX+4)
+    static constexpr int PW = HW + (sizeof(T) == 4 ? 4 : 2);
+    static constexpr int PH = TY + 2 * H;                  // staged y in [-H, TY+H)
+    static constexpr int SLOT = PH * PW;
+    static constexpr int NPHI = HAS_Z ? 4 : 1;             // Phi ring: planes p-2..p + prefetch
+    static constexpr int NCS = HAS_Z ? NST + 1 : 1;        // u ring
+    static constexpr int NC = HAS_Z ? 3 : 2;               // velocity components
+    static constexpr int NL = NST >= 2 ? (HAS_Z ? 3 : 1) : 0;   // L_U[Phi] ring (type D)
+    static constexpr int NP = NST >= 3 ? (HAS_Z ? 3 : 1) : 0;   // Psi ring
+    static constexpr size_t smem()
+    {
+        return sizeof(T) * (size_t)SLOT * (NPHI + NCS * NC + NP) + sizeof(D) * (size_t)SLOT * NL;
+    }
+};
+
+// Stage rows [r0, r0 + nr) x staged columns [-4, TX+4) of one plane.
+template <typename T, int NT, int TX, int PW, bool VEC>
+__device__ __forceinline__ void stage_rows(int tid, T *dst, const T *src, int x0, int y0, int r0, int nr, int H,
+                                           int nx, int ny)
+{
+    constexpr int HW = TX + 8;
+    if constexpr (VEC) {
+        constexpr int V = 16 / sizeof(T);
+        constexpr int CPR = HW / V;
+        for (int idx = tid; idx < nr * CPR; idx += NT) {
+            const int row = idx / CPR, cc = idx - (idx / CPR) * CPR;
+            const int gy = wrapi(y0 + r0 + row, ny);
+            const int gx = wrapi(x0 - 4 + cc * V, nx);
+            cp_async16(dst + (r0 + row + H) * PW + cc * V, src + (int64_t)gy * nx + gx);
+        }
+    } else {
+        for (int idx = tid; idx < nr * HW; idx += NT) {
+            const int row = idx / HW, col = idx - (idx / HW) * HW;
+            const int gy = wrapi(y0 + r0 + row, ny);
+            const int gx = wrapi(x0 - 4 + col, nx);
+            cp_async_elem(dst + (r0 + row + H) * PW + col, src + (int64_t)gy * nx + gx);
+        }
+    }
+}
+
+template <typename T, typename D, int NST, int TX, int TY, bool HAS_Z, bool VEC>
+__global__ void __launch_bounds__(256)
+k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ vel, Geo g)
+{
+    using K = Cfg<T, D, NST, TX, TY, HAS_Z>;
+    constexpr int NT = K::NT, H = K::H, PW = K::PW, SLOT = K::SLOT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sPhi = reinterpret_cast<T *>(smem_raw);                 // [NPHI][SLOT]
+    T *sC = sPhi + K::NPHI * SLOT;                             // [NCS][NC][SLOT]
+    T *sP = sC + K::NCS * K::NC * SLOT;                        // [NP][SLOT]
+    D *sL = reinterpret_cast<D *>(sP + K::NP * SLOT);          // [NL][SLOT]
+
+    const int tid = threadIdx.x;
+    const D sxd = D(g.sx), syd = D(g.sy), szd = D(g.sz);
+    const int nitems = g.tiles_x * g.tiles_y * g.chunks;
+    bool bad = false;
+
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int tx = item % g.tiles_x, rest = item / g.tiles_x;
+        const int x0 = tx * TX;
+        const int y0 = (rest % g.tiles_y) * TY;
+        const int z0 = (rest / g.tiles_y) * g.tz;
+        const int z1 = min(z0 + g.tz, g.nz);
+        const int pfirst = HAS_Z ? z0 - NST : 0;
+        const int plast = HAS_Z ? z1 + NST - 1 : 0;
+
+        auto issue = [&](int p) {
+            const int b = p - pfirst;
+            const int64_t base = (int64_t)wrapi(p, g.nz) * g.plane;
+            stage_rows<T, NT, TX, PW, VEC>(tid, sPhi + (b % K::NPHI) * SLOT, in + base, x0, y0, -H, TY + 2 * H, H,
+                                           g.nx, g.ny);
+            const int64_t bc = HAS_Z ? (int64_t)wrapi(p - 1, g.nz) * g.plane : base;
+            T *cdst = sC + (b % K::NCS) * K::NC * SLOT;
+#pragma unroll
+            for (int d = 0; d < K::NC; ++d)
+                stage_rows<T, NT, TX, PW, VEC>(tid, cdst + d * SLOT, vel + d * g.ncell + bc, x0, y0, -(H - 1),
+                                               TY + 2 * (H - 1), H, g.nx, g.ny);
+            cp_async_commit();
+        };
+        // ring slots of plane q
+        auto sl_phi = [&](int q) { return sPhi + ((q - pfirst) % K::NPHI) * SLOT; };
+        auto sl_c = [&](int q) { return sC + ((q + 1 - pfirst) % K::NCS) * K::NC * SLOT; };
+        auto sl_l = [&](int q) { return sL + (K::NL > 1 ? ((q + 1 - pfirst) % 3) : 0) * SLOT; };
+        auto sl_p = [&](int q) { return sP + (K::NP > 1 ? ((q + 1 - pfirst) % 3) : 0) * SLOT; };
+
+        issue(pfirst);
+        for (int p = pfirst; p <= plast; ++p) {
+            cp_async_wait_all();
+            __syncthreads();
+            if (p < plast) issue(p + 1);
+
+            // ------------------------------------------------ stage 1: L_U[Phi]
+            if (!HAS_Z || p >= z0 - NST + 2) {
+                const int q = HAS_Z ? p - 1 : 0;
+                constexpr int h = NST - 1;
+                constexpr int RW = TX + 2 * h, RH = TY + 2 * h;
+                const T *phi0 = sl_phi(q);
+                const T *cP = sl_c(q);
+                for (int r = tid; r < RW * RH; r += NT) {
+                    const int yy = r / RW, xx = r - (r / RW) * RW;
+                    const int o = (yy - h + H) * PW + (xx - h + 4);
+                    const D cx = D(cP[o]) * sxd, cy = D(cP[SLOT + o]) * syd;
+                    const D cz = HAS_Z ? D(cP[2 * SLOT + o]) * szd : D(0);
+                    const int ox = cx > D(0) ? -1 : 1, oy = cy > D(0) ? -PW : PW;
+                    const T *phi1 = HAS_Z ? (cz > D(0) ? sl_phi(q - 1) : sl_phi(q + 1)) : phi0;
+                    const D v = mlerp<D, HAS_Z>(phi0, phi1, o, ox, oy, fabs(cx), fabs(cy), fabs(cz));
+                    if constexpr (NST == 1) {
+                        bad |= fabs(cx) > D(1) || fabs(cy) > D(1) || fabs(cz) > D(1);
+                        const int gx = x0 + xx, gy = y0 + yy;
+                        if (gx < g.nx && gy < g.ny) out[(int64_t)q * g.plane + (int64_t)gy * g.nx + gx] = T(v);
+                    } else {
+                        sl_l(q)[o] = v;
+                    }
+                }
+            }
+            if constexpr (NST >= 2) {
+                __syncthreads();
+                // -------------------------------- stage 2: Phi_bar and the correction
+                if (!HAS_Z || p >= z0 - NST + 4) {
+                    const int q = HAS_Z ? p - 2 : 0;
+                    constexpr int h = NST - 2;
+                    constexpr int RW = TX + 2 * h, RH = TY + 2 * h;
+                    const T *phiq = sl_phi(q);
+                    const T *cP = sl_c(q);
+                    const D *l0 = sl_l(q);
+                    for (int r = tid; r < RW * RH; r += NT) {
+                        const int yy = r / RW, xx = r - (r / RW) * RW;
+                        const int o = (yy - h + H) * PW + (xx - h + 4);
+                        const D cx = D(cP[o]) * sxd, cy = D(cP[SLOT + o]) * syd;
+                        const D cz = HAS_Z ? D(cP[2 * SLOT + o]) * szd : D(0);
+                        // reversed flow: departure x + u dt, corners toward +s
+                        const int ox = cx > D(0) ? 1 : -1, oy = cy > D(0) ? PW : -PW;
+                        const D *l1 = HAS_Z ? (cz > D(0) ? sl_l(q + 1) : sl_l(q - 1)) : l0;
+                        const D bar = mlerp<D, HAS_Z>(l0, l1, o, ox, oy, fabs(cx), fabs(cy), fabs(cz));
+                        const D delta = D(phiq[o]) - bar;
+                        if constexpr (NST == 2) {
+                            bad |= fabs(cx) > D(1) || fabs(cy) > D(1) || fabs(cz) > D(1);
+                            const int gx = x0 + xx, gy = y0 + yy;
+                            if (gx < g.nx && gy < g.ny)
+                                out[(int64_t)q * g.plane + (int64_t)gy * g.nx + gx] = T(l0[o] + delta * D(0.5));
+                        } else {
+                            sl_p(q)[o] = T(D(phiq[o]) + delta * D(0.5));
+                        }
+                    }
+                }
+            }
+            if constexpr (NST >= 3) {
+                __syncthreads();
+                // -------------------------------------------- stage 3: L_U[Psi]
+                if (!HAS_Z || p >= z0 + 3) {
+                    const int q = HAS_Z ? p - 3 : 0;
+                    const T *cP = sl_c(q);
+                    const T *p0 = sl_p(q);
+                    for (int r = tid; r < TX * TY; r += NT) {
+                        const int yy = r / TX, xx = r - (r / TX) * TX;
+                        const int o = (yy + H) * PW + (xx + 4);
+                        const T cx = T(D(cP[o]) * sxd), cy = T(D(cP[SLOT + o]) * syd);
+                        const T cz = HAS_Z ? T(D(cP[2 * SLOT + o]) * szd) : T(0);
+                        bad |= fabs(cx) > T(1) || fabs(cy) > T(1) || fabs(cz) > T(1);
+                        const int ox = cx > T(0) ? -1 : 1, oy = cy > T(0) ? -PW : PW;
+                        const T *p1 = HAS_Z ? (cz > T(0) ? sl_p(q - 1) : sl_p(q + 1)) : p0;
+                        const T v = mlerp<T, HAS_Z>(p0, p1, o, ox, oy, fabs(cx), fabs(cy), fabs(cz));
+                        const int gx = x0 + xx, gy = y0 + yy;
+                        if (gx < g.nx && gy < g.ny) out[(int64_t)q * g.plane + (int64_t)gy * g.nx + gx] = v;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    flag_cfl(g.status, bad);
+}
+
+template <typename T, typename D, int NST, int TX, int TY, bool HAS_Z, bool VEC>
+cudaError_t go(Geo g, int grid, const void *in, void *out, const void *vel, cudaStream_t st)
+{
+    using K = Cfg<T, D, NST, TX, TY, HAS_Z>;
+    auto kern = k_unsplit<T, D, NST, TX, TY, HAS_Z, VEC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::smem());
+    if (e != cudaSuccess) return e;
+    g.tiles_y = (g.ny + TY - 1) / TY;
+    const int nitems = g.tiles_x * g.tiles_y * g.chunks;
+    const int gr = grid > 0 && grid < nitems ? grid : nitems;
+    kern<<<gr, K::NT, K::smem(), st>>>(static_cast<const T *>(in), static_cast<T *>(out),
+                                       static_cast<const T *>(vel), g);
+    return cudaGetLastError();
+}
+
+template <typename T, typename D, int TY, bool HAS_Z, bool VEC>
+cudaError_t by_scheme(int scheme, const Geo &g, int grid, const void *in, void *out, const void *vel, cudaStream_t st)
+{
+    switch (scheme) {
+    case 0: return go<T, D, 1, 32, TY, HAS_Z, VEC>(g, grid, in, out, vel, st);
+    case 1: return go<T, D, 2, 32, TY, HAS_Z, VEC>(g, grid, in, out, vel, st);
+    default: return go<T, D, 3, 32, TY, HAS_Z, VEC>(g, grid, in, out, vel, st);
+    }
+}
+
+template <typename T, typename D, int TY>
+cudaError_t by_shape(int scheme, bool has_z, bool vec, const Geo &g, int grid, const void *in, void *out,
+                     const void *vel, cudaStream_t st)
+{
+    if (has_z)
+        return vec ? by_scheme<T, D, TY, true, true>(scheme, g, grid, in, out, vel, st)
+                   : by_scheme<T, D, TY, true, false>(scheme, g, grid, in, out, vel, st);
+    return vec ? by_scheme<T, D, TY, false, true>(scheme, g, grid, in, out, vel, st)
+               : by_scheme<T, D, TY, false, false>(scheme, g, grid, in, out, vel, st);
+}
+
+}  // namespace
+
+cudaError_t launch_unsplit(int dtype, int scheme, const void *in, void *out, const void *vel, int ndim,
+                           const int64_t dims[3], const double s[3], Launch lc, unsigned *status, cudaStream_t st)
+{
+    Geo g;
+    g.nx = (int)dims[0];
+    g.ny = (int)dims[1];
+    g.nz = ndim == 3 ? (int)dims[2] : 1;
+    g.plane = (int64_t)g.nx * g.ny;
+    g.ncell = g.plane * g.nz;
+    g.sx = s[0];
+    g.sy = s[1];
+    g.sz = ndim == 3 ? s[2] : 0.0;
+    g.status = status;
+    g.tz = ndim == 3 ? (lc.tz > 0 ? lc.tz : default_tz(dtype, ndim, dims)) : 1;
+    if (g.tz > g.nz) g.tz = g.nz;
+    g.chunks = (g.nz + g.tz - 1) / g.tz;
+    g.tiles_x = (g.nx + 31) / 32;
+    const bool has_z = ndim == 3;
+    if (dtype == 1) return by_shape<double, double, 8>(scheme, has_z, lc.aligned && g.nx % 2 == 0, g, lc.grid, in, out, vel, st);
+    if (dtype == 2) return by_shape<float, double, 16>(scheme, has_z, lc.aligned && g.nx % 4 == 0, g, lc.grid, in, out, vel, st);
+    return by_shape<float, float, 16>(scheme, has_z, lc.aligned && g.nx % 4 == 0, g, lc.grid, in, out, vel, st);
+}
+
+}  // namespace sl

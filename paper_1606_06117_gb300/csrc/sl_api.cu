@@ -1,0 +1,458 @@
+// sl_api.cu -- the extern "C" entry points of libsl (declared in include/sl.h):
+// argument validation, the per-device context, error reporting and dispatch
+// to the fused kernels.  No C++ exception crosses these functions.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "sl.h"
+#include "sl_internal.h"
+
+namespace sl {
+namespace {
+
+thread_local std::string g_err;
+std::mutex g_mu;
+constexpr int kMaxDev = 64;
+DevCtx g_ctx[kMaxDev];
+
+struct Staging {
+    void *buf = nullptr;
+    size_t bytes = 0;
+};
+Staging g_stage[kMaxDev];
+
+// autotuned z chunk per (nx, ny, nz, dtype)
+std::map<std::tuple<int64_t, int64_t, int64_t, int>, int> g_tuned;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(SL_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t elem_size(int dtype) { return dtype == SL_F64 ? 8 : 4; }
+
+bool overlap(const void *a, size_t na, const void *b, size_t nb)
+{
+    const char *pa = static_cast<const char *>(a), *pb = static_cast<const char *>(b);
+    return pa < pb + nb && pb < pa + na;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Validates the geometry arguments shared by the step entry points and
+// computes Courant scale factors s_d = dt / dx_d.
+int check_geometry(int ndim, const int64_t dims[3], const double spacing[3], double dt, int dtype, double s[3])
+{
+    if (ndim != 2 && ndim != 3) return fail(SL_ERR_ARG, "ndim must be 2 or 3 (got %d)", ndim);
+    if (!dims || !spacing) return fail(SL_ERR_ARG, "dims and spacing must not be NULL");
+    if (dtype < SL_F32 || dtype > SL_F32_D64) return fail(SL_ERR_ARG, "unknown dtype %d", dtype);
+    for (int d = 0; d < 3; ++d)
+        if (dims[d] < 1 || dims[d] > (int64_t)1 << 30) return fail(SL_ERR_ARG, "dims[%d] = %lld out of range", d, (long long)dims[d]);
+    if (ndim == 2 && dims[2] != 1) return fail(SL_ERR_ARG, "dims[2] must be 1 when ndim = 2");
+    if (dims[0] * dims[1] > ((int64_t)1 << 31) - 1) return fail(SL_ERR_ARG, "an x-y plane must hold fewer than 2^31 cells");
+    if (dims[0] * dims[1] * dims[2] > ((int64_t)1 << 40)) return fail(SL_ERR_ARG, "grid too large");
+    if (!std::isfinite(dt)) return fail(SL_ERR_ARG, "dt must be finite");
+    for (int d = 0; d < ndim; ++d) {
+        if (!(spacing[d] > 0.0) || !std::isfinite(spacing[d])) return fail(SL_ERR_ARG, "spacing[%d] must be > 0", d);
+        s[d] = dt / spacing[d];
+    }
+    if (ndim == 2) s[2] = 0.0;
+    return SL_OK;
+}
+
+int64_t ncell_of(const int64_t dims[3]) { return dims[0] * dims[1] * dims[2]; }
+
+int launch_step(void *out, const void *in, const void *vel, int ndim, const int64_t dims[3], const double s[3],
+                int scheme, int dtype, int parity, cudaStream_t st, DevCtx *c)
+{
+    Launch lc;
+    lc.aligned = aligned16(out) && aligned16(in) && aligned16(vel);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_tuned.find(std::make_tuple(dims[0], dims[1], dims[2], dtype));
+        if (it != g_tuned.end()) lc.tz = it->second;
+    }
+    cudaError_t e = scheme == SL_CEC ? launch_split_cec(dtype, in, out, vel, ndim, dims, s, parity, lc, c->status, st)
+                                     : launch_unsplit(dtype, scheme, in, out, vel, ndim, dims, s, lc, c->status, st);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return SL_OK;
+}
+
+}  // namespace
+
+DevCtx *ctx_get()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevCtx &c = g_ctx[dev];
+    if (c.device == dev) return &c;
+    void *p = nullptr;
+    const size_t bytes = 256 + sizeof(double) * (kReduceBlocks + 1) * 4 + 256 * sizeof(unsigned);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    if (cudaMemset(p, 0, bytes) != cudaSuccess) {
+        cudaFree(p);
+        return nullptr;
+    }
+    c.status = static_cast<unsigned *>(p);
+    c.partials = reinterpret_cast<double *>(static_cast<char *>(p) + 256);
+    c.counters = reinterpret_cast<unsigned *>(c.partials + (kReduceBlocks + 1) * 4);
+    cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    c.device = dev;
+    return &c;
+}
+
+}  // namespace sl
+
+using namespace sl;
+
+struct sl_batch {
+    int device = -1;
+    int n = 0;
+    int scheme = SL_CEC;
+    int dtype = SL_F32;
+    BatchRec *dev_recs = nullptr;
+    unsigned *counter = nullptr;
+    int nitems[2] = {0, 0};
+    int grid[2] = {0, 0};
+};
+
+extern "C" {
+
+int sl_version(void) { return 10000; }
+
+const char *sl_last_error(void) { return g_err.c_str(); }
+
+int sl_init(void)
+{
+    if (!ctx_get()) return fail(SL_ERR_CUDA, "could not create the device context");
+    return SL_OK;
+}
+
+int sl_advect(void *out, const void *in, const void *vel, int ndim, const int64_t dims[3], const double spacing[3],
+              double dt, int scheme, int dtype, int step_parity, void *stream)
+{
+    if (!out || !in || !vel) return fail(SL_ERR_ARG, "out, in and vel must not be NULL");
+    if (scheme < SL_CIR || scheme > SL_CEC) return fail(SL_ERR_ARG, "unknown scheme %d", scheme);
+    double s[3];
+    int rc = check_geometry(ndim, dims, spacing, dt, dtype, s);
+    if (rc) return rc;
+    const size_t es = elem_size(dtype);
+    const size_t fb = (size_t)ncell_of(dims) * es;
+    if (overlap(out, fb, in, fb)) return fail(SL_ERR_ALIAS, "out overlaps in");
+    if (overlap(out, fb, vel, fb * ndim)) return fail(SL_ERR_ALIAS, "out overlaps vel");
+    DevCtx *c = ctx_get();
+    if (!c) return fail(SL_ERR_CUDA, "could not create the device context");
+    return launch_step(out, in, vel, ndim, dims, s, scheme, dtype, step_parity, static_cast<cudaStream_t>(stream), c);
+}
+
+int sl_advect_multi(void *const *outs, const void *const *ins, int nfields, const void *vel, int ndim,
+                    const int64_t dims[3], const double spacing[3], double dt, int scheme, int dtype,
+                    int step_parity, void *stream)
+{
+    if (!outs || !ins || nfields < 1) return fail(SL_ERR_ARG, "outs/ins must hold nfields >= 1 pointers");
+    if (!vel) return fail(SL_ERR_ARG, "vel must not be NULL");
+    if (scheme < SL_CIR || scheme > SL_CEC) return fail(SL_ERR_ARG, "unknown scheme %d", scheme);
+    double s[3];
+    int rc = check_geometry(ndim, dims, spacing, dt, dtype, s);
+    if (rc) return rc;
+    const size_t fb = (size_t)ncell_of(dims) * elem_size(dtype);
+    for (int f = 0; f < nfields; ++f) {
+        if (!outs[f] || !ins[f]) return fail(SL_ERR_ARG, "field %d pointer is NULL", f);
+        if (overlap(outs[f], fb, vel, fb * ndim)) return fail(SL_ERR_ALIAS, "outs[%d] overlaps vel", f);
+        for (int h = 0; h < nfields; ++h) {
+            if (overlap(outs[f], fb, ins[h], fb)) return fail(SL_ERR_ALIAS, "outs[%d] overlaps ins[%d]", f, h);
+            if (h != f && overlap(outs[f], fb, outs[h], fb)) return fail(SL_ERR_ALIAS, "outs[%d] overlaps outs[%d]", f, h);
+        }
+    }
+    DevCtx *c = ctx_get();
+    if (!c) return fail(SL_ERR_CUDA, "could not create the device context");
+    for (int f = 0; f < nfields; ++f) {
+        rc = launch_step(outs[f], ins[f], vel, ndim, dims, s, scheme, dtype, step_parity,
+                         static_cast<cudaStream_t>(stream), c);
+        if (rc) return rc;
+    }
+    return SL_OK;
+}
+
+int sl_advect_host(void *out, const void *in, const void *vel, int ndim, const int64_t dims[3],
+                   const double spacing[3], double dt, int scheme, int dtype, int step_parity, void *stream)
+{
+    if (!out || !in || !vel) return fail(SL_ERR_ARG, "out, in and vel must not be NULL");
+    if (scheme < SL_CIR || scheme > SL_CEC) return fail(SL_ERR_ARG, "unknown scheme %d", scheme);
+    double s[3];
+    int rc = check_geometry(ndim, dims, spacing, dt, dtype, s);
+    if (rc) return rc;
+    const size_t fb = (size_t)ncell_of(dims) * elem_size(dtype);
+    if (overlap(out, fb, in, fb) || overlap(out, fb, vel, fb * ndim)) return fail(SL_ERR_ALIAS, "out overlaps an input");
+    DevCtx *c = ctx_get();
+    if (!c) return fail(SL_ERR_CUDA, "could not create the device context");
+    const size_t need = fb * (2 + ndim) + 512;
+    Staging &sg = g_stage[c->device];
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (sg.bytes < need) {
+            if (sg.buf) cudaFree(sg.buf);
+            sg.buf = nullptr;
+            sg.bytes = 0;
+            if (cudaMalloc(&sg.buf, need) != cudaSuccess) return fail(SL_ERR_NOMEM, "device staging of %zu bytes", need);
+            sg.bytes = need;
+        }
+    }
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    char *base = static_cast<char *>(sg.buf);
+    void *d_in = base;
+    void *d_out = base + al(fb);
+    void *d_vel = base + 2 * al(fb);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(d_in, in, fb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_vel, vel, fb * ndim, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
+    rc = launch_step(d_out, d_in, d_vel, ndim, dims, s, scheme, dtype, step_parity, st, c);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(out, d_out, fb, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
+    return SL_OK;
+}
+
+int sl_release_host_staging(void)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return fail(SL_ERR_CUDA, "no device");
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_stage[dev].buf) cudaFree(g_stage[dev].buf);
+    g_stage[dev] = Staging();
+    return SL_OK;
+}
+
+int sl_courant_max(const void *vel, int ndim, const int64_t dims[3], const double spacing[3], double dt, int dtype,
+                   double *out_max, void *stream)
+{
+    if (!vel || !out_max) return fail(SL_ERR_ARG, "vel and out_max must not be NULL");
+    double s[3];
+    int rc = check_geometry(ndim, dims, spacing, dt, dtype, s);
+    if (rc) return rc;
+    DevCtx *c = ctx_get();
+    if (!c) return fail(SL_ERR_CUDA, "could not create the device context");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_courant(dtype == SL_F64 ? 1 : 0, vel, ndim, ncell_of(dims), s, c->partials, st);
+    double res[4];
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(res, c->partials + kReduceBlocks * 4, sizeof res, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "courant reduction");
+    *out_max = res[1];
+    return SL_OK;
+}
+
+int sl_norms(const void *a, const void *b, int64_t n, int dtype, double out[3], void *stream)
+{
+    if (!a || !b || !out || n < 1) return fail(SL_ERR_ARG, "a, b, out must be non-NULL and n >= 1");
+    if (dtype < SL_F32 || dtype > SL_F32_D64) return fail(SL_ERR_ARG, "unknown dtype %d", dtype);
+    DevCtx *c = ctx_get();
+    if (!c) return fail(SL_ERR_CUDA, "could not create the device context");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_norms(dtype == SL_F64 ? 1 : 0, a, b, n, c->partials, st);
+    double res[4];
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(res, c->partials + kReduceBlocks * 4, sizeof res, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "norm reduction");
+    out[0] = std::sqrt(res[0] / (double)n);
+    out[1] = res[1];
+    out[2] = res[2] > 0.0 ? std::sqrt(res[0] / res[2]) : std::sqrt(res[0]);
+    return SL_OK;
+}
+
+int sl_device_status(void *stream, unsigned *out_bits)
+{
+    if (!out_bits) return fail(SL_ERR_ARG, "out_bits must not be NULL");
+    DevCtx *c = ctx_get();
+    if (!c) return fail(SL_ERR_CUDA, "could not create the device context");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, c->status, sizeof v, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof v, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    *out_bits = v;
+    return SL_OK;
+}
+
+int sl_batch_create(sl_batch **out, const sl_instance *inst, int n, int scheme, int dtype, int tile_z)
+{
+    if (!out || !inst || n < 1) return fail(SL_ERR_ARG, "out and inst must be non-NULL and n >= 1");
+    *out = nullptr;
+    if (scheme != SL_CEC || dtype != SL_F32)
+        return fail(SL_ERR_UNSUPPORTED, "batched steps serve SL_CEC with SL_F32");
+    DevCtx *c = ctx_get();
+    if (!c) return fail(SL_ERR_CUDA, "could not create the device context");
+    std::vector<BatchRec> recs(n);
+    int total[2] = {0, 0};
+    for (int i = 0; i < n; ++i) {
+        const sl_instance &in = inst[i];
+        double s[3];
+        int rc = check_geometry(3, in.dims, in.spacing, in.dt, dtype, s);
+        if (rc) return rc;
+        if (!in.a || !in.b || !in.vel) return fail(SL_ERR_ARG, "instance %d has a NULL pointer", i);
+        if (in.dims[0] % 4 || !aligned16(in.a) || !aligned16(in.b) || !aligned16(in.vel))
+            return fail(SL_ERR_UNSUPPORTED, "instance %d: batched steps need dims[0] %% 4 == 0 and 16-byte aligned buffers", i);
+        const size_t fb = (size_t)ncell_of(in.dims) * 4;
+        if (overlap(in.a, fb, in.b, fb) || overlap(in.b, fb, in.vel, 3 * fb) || overlap(in.a, fb, in.vel, 3 * fb))
+            return fail(SL_ERR_ALIAS, "instance %d: buffers overlap", i);
+        BatchRec &r = recs[i];
+        r.a = in.a;
+        r.b = in.b;
+        r.vel = in.vel;
+        for (int par = 0; par < 2; ++par) {
+            int tx, ty;
+            batched_tiles(par, tx, ty);
+            Geo &g = r.g[par];
+            g.nx = (int)in.dims[0];
+            g.ny = (int)in.dims[1];
+            g.nz = (int)in.dims[2];
+            g.plane = (int64_t)g.nx * g.ny;
+            g.ncell = g.plane * g.nz;
+            g.sx = s[0];
+            g.sy = s[1];
+            g.sz = s[2];
+            g.status = c->status;
+            g.tz = tile_z > 0 ? std::min(tile_z, g.nz) : std::min(32, g.nz);
+            g.chunks = (g.nz + g.tz - 1) / g.tz;
+            g.tiles_x = (g.nx + tx - 1) / tx;
+            g.tiles_y = (g.ny + ty - 1) / ty;
+            r.item0[par] = total[par];
+            total[par] += g.tiles_x * g.tiles_y * g.chunks;
+        }
+    }
+    sl_batch *b = new (std::nothrow) sl_batch();
+    if (!b) return fail(SL_ERR_NOMEM, "host allocation");
+    b->device = c->device;
+    b->n = n;
+    b->scheme = scheme;
+    b->dtype = dtype;
+    b->nitems[0] = total[0];
+    b->nitems[1] = total[1];
+    for (int par = 0; par < 2; ++par) b->grid[par] = std::min(total[par], c->num_sms * batched_blocks_per_sm(par));
+    void *p = nullptr;
+    if (cudaMalloc(&p, sizeof(BatchRec) * n + 256) != cudaSuccess) {
+        delete b;
+        return fail(SL_ERR_NOMEM, "device instance table");
+    }
+    b->counter = static_cast<unsigned *>(p);
+    b->dev_recs = reinterpret_cast<BatchRec *>(static_cast<char *>(p) + 256);
+    cudaError_t e = cudaMemcpy(b->dev_recs, recs.data(), sizeof(BatchRec) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->counter, 0, 256);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        delete b;
+        return cuda_fail(e, "instance table upload");
+    }
+    *out = b;
+    return SL_OK;
+}
+
+int sl_batch_step(sl_batch *b, int step_index, void *stream)
+{
+    if (!b) return fail(SL_ERR_ARG, "batch is NULL");
+    DevCtx *c = ctx_get();
+    if (!c) return fail(SL_ERR_CUDA, "could not create the device context");
+    if (c->device != b->device) return fail(SL_ERR_ARG, "batch belongs to device %d", b->device);
+    const int par = step_index & 1;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess)
+        e = launch_batched_cec(b->dev_recs, b->n, b->nitems[par], par, b->counter, c->status, b->grid[par], st);
+    if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+    return SL_OK;
+}
+
+int sl_batch_destroy(sl_batch *b)
+{
+    if (!b) return SL_OK;
+    if (b->counter) cudaFree(b->counter);
+    delete b;
+    return SL_OK;
+}
+
+int sl_autotune(void *out, const void *in, const void *vel, int ndim, const int64_t dims[3], const double spacing[3],
+                double dt, int dtype, int *tile_z, void *stream)
+{
+    if (!out || !in || !vel || !tile_z) return fail(SL_ERR_ARG, "NULL argument");
+    double s[3];
+    int rc = check_geometry(ndim, dims, spacing, dt, dtype, s);
+    if (rc) return rc;
+    const size_t fb = (size_t)ncell_of(dims) * elem_size(dtype);
+    if (overlap(out, fb, in, fb) || overlap(out, fb, vel, fb * ndim)) return fail(SL_ERR_ALIAS, "out overlaps an input");
+    DevCtx *c = ctx_get();
+    if (!c) return fail(SL_ERR_CUDA, "could not create the device context");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (ndim == 2) {
+        *tile_z = 1;
+        return SL_OK;
+    }
+    std::vector<int> cands;
+    for (int tz : {8, 16, 24, 32, 48, 64, 96, 128, 192, 256})
+        if (tz <= dims[2]) cands.push_back(tz);
+    if (cands.empty() || cands.back() != (int)dims[2]) cands.push_back((int)dims[2]);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(SL_ERR_CUDA, "events");
+    float best = 1e30f;
+    int best_tz = cands.front();
+    Launch lc;
+    lc.aligned = aligned16(out) && aligned16(in) && aligned16(vel);
+    for (int tz : cands) {
+        lc.tz = tz;
+        float tot = 0.0f;
+        cudaError_t e = cudaSuccess;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+            e = launch_split_cec(dtype, in, out, vel, ndim, dims, s, rep, lc, c->status, st);   // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) e = launch_split_cec(dtype, in, out, vel, ndim, dims, s, rep, lc, c->status, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            tot += ms;
+        }
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(e, "autotune");
+        }
+        if (tot < best) {
+            best = tot;
+            best_tz = tz;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_tuned[std::make_tuple(dims[0], dims[1], dims[2], dtype)] = best_tz;
+    }
+    *tile_z = best_tz;
+    return SL_OK;
+}
+
+}  // extern "C"

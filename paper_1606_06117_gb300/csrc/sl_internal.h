@@ -1,0 +1,63 @@
+// sl_internal.h -- declarations shared by the host entry points and the kernel
+// translation units of libsl.  Not part of the public ABI (see include/sl.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sl_common.cuh"
+
+namespace sl {
+
+// Per-device context: status word and small work areas.
+struct DevCtx {
+    int device = -1;
+    unsigned *status = nullptr;      // SL_DEV_* bits
+    double *partials = nullptr;      // reduction partials (kReduceBlocks x 4)
+    unsigned *counters = nullptr;    // work counters for batched launches
+    int num_sms = 0;
+};
+
+constexpr int kReduceBlocks = 1024;
+
+DevCtx *ctx_get();   // context of the current device, created on demand
+
+// Launch configuration chosen for a fused kernel.
+struct Launch {
+    int tz = 0;          // z chunk (planes per work item); 0 = default
+    int grid = 0;        // CTAs; 0 = one per item
+    bool aligned = true; // all base pointers 16-byte aligned (vector staging allowed)
+};
+
+// Fused single-step kernels; return a cudaError_t of the launch.
+cudaError_t launch_split_cec(int dtype, const void *in, void *out, const void *vel, int ndim,
+                             const int64_t dims[3], const double s[3], int parity,
+                             Launch lc, unsigned *status, cudaStream_t st);
+cudaError_t launch_unsplit(int dtype, int scheme, const void *in, void *out, const void *vel,
+                           int ndim, const int64_t dims[3], const double s[3], Launch lc,
+                           unsigned *status, cudaStream_t st);
+
+// Reductions (synchronous results through host pointers after a stream sync).
+cudaError_t launch_norms(int dtype, const void *a, const void *b, int64_t n, double *partials,
+                         cudaStream_t st);
+cudaError_t launch_courant(int dtype, const void *vel, int ndim, int64_t n, const double s[3],
+                           double *partials, cudaStream_t st);
+
+// Batched persistent CEC step (FP32, 3D) over an instance table in device
+// memory.  Record i owns global items [item0[par], item0[par] + items) of the
+// x,y,z (par 0) or z,y,x (par 1) decomposition.
+struct BatchRec {
+    void *a;
+    void *b;
+    const void *vel;
+    Geo g[2];
+    int item0[2];
+};
+void batched_tiles(int parity, int &tx, int &ty);
+int batched_blocks_per_sm(int parity);
+cudaError_t launch_batched_cec(const BatchRec *dev_recs, int ninst, int nitems, int parity, unsigned *counter,
+                               unsigned *status, int grid, cudaStream_t st);
+
+int default_tz(int dtype, int ndim, const int64_t dims[3]);
+
+}  // namespace sl

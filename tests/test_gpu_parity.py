@@ -1,0 +1,220 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bar: relative L2 <= 1e-5 for float32 fields, <= 1e-12 for float64 fields,
+element-wise against the oracle on the same seeded inputs; sizes span several
+tiles, z chunks and ragged tails; full-size grids are checked on sampled cells.
+"""
+import math
+import zlib
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import (TOL, TORCH_DT, courant, oracle_at_cells, oracle_step, random_case, rel_l2,
+                         sample_cells)
+from oracle import oracle as O
+from paper_1606_06117_gb300 import _lib as sl
+from paper_1606_06117_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+SHAPES_3D = [(5, 5, 5), (11, 9, 7), (37, 45, 68), (9, 10, 12), (3, 4, 40)]
+SHAPES_2D = [(13, 17), (40, 64), (1, 8)]
+SCHEMES = ["CIR", "FEC", "BEC", "CEC"]
+
+
+def gpu_step(phi, vel, spacing, dt, scheme, parity, dtype):
+    return sl.advect(phi.to(DEV), vel.to(DEV), dt, spacing, scheme, parity, delta64=(dtype == "f32_d64"))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "f32_d64"])
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("shape", SHAPES_3D + SHAPES_2D)
+def test_one_step_matches_oracle(shape, scheme, dtype):
+    phi, vel, sp, dt = random_case(shape, seed=zlib.crc32(repr((shape, scheme)).encode()) % 1000, dtype=dtype)
+    for parity in ((0, 1) if scheme == "CEC" else (0,)):
+        out = gpu_step(phi, vel, sp, dt, scheme, parity, dtype)
+        torch.cuda.synchronize()
+        ref = oracle_step(phi, vel, sp, dt, scheme, parity)
+        err = rel_l2(out.cpu().double().numpy(), ref)
+        assert err <= TOL[dtype], f"{scheme} {dtype} {shape} parity {parity}: rel L2 {err:.3e}"
+    assert sl.sl_device_status() == 0
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_many_steps_smooth_flow(scheme, dtype):
+    """20 steps of an ABC flow on a random-mode field (sweep order alternating)."""
+    shape = (24, 28, 36)
+    t = TORCH_DT[dtype]
+    phi = W.random_modes(shape, W.draw_modes(3, 16, 4, seed=2), dtype=t)
+    vel = W.abc_velocity(shape, dtype=t)
+    sp = [2 * math.pi / n for n in shape[::-1]]
+    dt = 0.8 * min(sp) / 2.0
+    ref = phi.double().numpy()
+    cur = phi.to(DEV)
+    v = vel.to(DEV)
+    c = courant(vel, sp, dt)
+    for k in range(20):
+        cur = sl.advect(cur, v, dt, sp, scheme, k)
+        ref = O.step(ref, c, O.SCHEMES[scheme], k)
+    err = rel_l2(cur.cpu().double().numpy(), ref)
+    assert err <= 4 * TOL[dtype], err
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_constant_field_is_preserved_bitwise(scheme, dtype):
+    shape = (10, 12, 16)
+    _, vel, sp, dt = random_case(shape, seed=3, dtype=dtype)
+    phi = torch.full(shape, 1.625, dtype=TORCH_DT[dtype])
+    for parity in (0, 1):
+        out = gpu_step(phi, vel, sp, dt, scheme, parity, dtype).cpu()
+        assert torch.equal(out, phi)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_integer_courant_is_a_shift(scheme):
+    shape = (8, 12, 16)
+    rng = np.random.default_rng(4)
+    phi = torch.from_numpy(rng.standard_normal(shape)).float()
+    sp, dt = [1.0, 1.0, 1.0], 1.0
+    vel = torch.stack([torch.full(shape, v) for v in (1.0, -1.0, 1.0)]).float()
+    out = gpu_step(phi, vel, sp, dt, scheme, 0, "f32").cpu()
+    ref = torch.roll(phi, shifts=(1, -1, 1), dims=(0, 1, 2))
+    assert torch.allclose(out, ref, atol=1e-6, rtol=0)
+
+
+def test_courant_violation_sets_status_bit():
+    shape = (8, 8, 8)
+    phi, vel, sp, dt = random_case(shape, seed=5, cmax=0.5)
+    vel[0, 3, 4, 5] = 1.5 * sp[0] / dt
+    sl.sl_device_status()   # clear
+    out = gpu_step(phi, vel, sp, dt, "CEC", 0, "f32")
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all()
+    assert sl.sl_device_status() & sl.DEV_CFL
+    assert sl.sl_device_status() == 0   # read clears
+
+
+def test_argument_errors():
+    shape = (8, 8, 8)
+    phi, vel, sp, dt = random_case(shape, seed=6)
+    p, v = phi.to(DEV), vel.to(DEV)
+    dims = [8, 8, 8]
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_advect(p, p, v, 3, dims, sp, dt, sl.CEC, sl.F32)
+    assert e.value.code == -2
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_advect(torch.empty_like(p), p, v, 4, dims, sp, dt, sl.CEC, sl.F32)
+    assert e.value.code == -1
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_advect(torch.empty_like(p), p, v, 3, [8, 0, 8], sp, dt, sl.CEC, sl.F32)
+    assert e.value.code == -1
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_advect(torch.empty_like(p), p, v, 3, dims, sp, dt, 7, sl.F32)
+    assert e.value.code == -1
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_advect(torch.empty_like(p), p, v, 3, dims, [0.1, -1.0, 0.1], dt, sl.CEC, sl.F32)
+    assert e.value.code == -1
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_advect(v[0], p, v, 3, dims, sp, dt, sl.CEC, sl.F32)
+    assert e.value.code == -2
+
+
+def test_unaligned_pointers_use_the_scalar_staging():
+    shape = (6, 8, 12)
+    phi, vel, sp, dt = random_case(shape, seed=7)
+    n = phi.numel()
+    buf = torch.empty(n + 1, device=DEV)
+    buf[1:] = phi.to(DEV).reshape(-1)
+    out = torch.empty(n + 1, device=DEV)
+    sl.sl_advect(out[1:], buf[1:], vel.to(DEV), 3, [12, 8, 6], sp, dt, sl.CEC, sl.F32, 0)
+    torch.cuda.synchronize()
+    ref = oracle_step(phi, vel, sp, dt, "CEC", 0)
+    assert rel_l2(out[1:].reshape(shape).cpu().double().numpy(), ref) <= 1e-5
+
+
+def test_multi_field_equals_single_calls():
+    shape = (12, 16, 20)
+    _, vel, sp, dt = random_case(shape, seed=8)
+    v = vel.to(DEV)
+    fields = [torch.randn(shape, device=DEV) for _ in range(4)]
+    outs = [torch.empty_like(f) for f in fields]
+    sl.sl_advect_multi(outs, fields, v, 3, [20, 16, 12], sp, dt, sl.CEC, sl.F32, 1)
+    for f, o in zip(fields, outs):
+        assert torch.equal(o, sl.advect(f, v, dt, sp, "CEC", 1))
+
+
+def test_host_buffers_equal_device_path():
+    shape = (16, 20, 24)
+    phi, vel, sp, dt = random_case(shape, seed=9)
+    out = torch.empty_like(phi).pin_memory()
+    sl.sl_advect_host(out, phi.pin_memory(), vel.pin_memory(), 3, [24, 20, 16], sp, dt, sl.BEC, sl.F32, 0)
+    assert torch.equal(out, sl.advect(phi.to(DEV), vel.to(DEV), dt, sp, "BEC", 0).cpu())
+
+
+def test_norms_and_courant_reductions():
+    shape = (30, 40, 50)
+    a = torch.randn(shape, dtype=torch.float64, device=DEV)
+    b = torch.randn(shape, dtype=torch.float64, device=DEV)
+    got = sl.sl_norms(a, b, a.numel(), sl.F64)
+    ref = O.norms(a.cpu().numpy(), b.cpu().numpy())
+    assert np.allclose(got, ref, rtol=1e-12, atol=0)
+    phi, vel, sp, dt = random_case(shape, seed=10, cmax=0.7)
+    cmax = sl.sl_courant_max(vel.to(DEV), 3, [50, 40, 30], sp, dt, sl.F32)
+    assert cmax == pytest.approx(np.abs(courant(vel, sp, dt)).max(), rel=1e-15)
+
+
+@pytest.mark.parametrize("shape,parity", [((256, 256, 256), 0), ((256, 256, 256), 1)])
+def test_full_size_sampled_parity(shape, parity):
+    """The benchmark workload (256^3 ABC flow, 32-mode field, CFL 0.8) at full size in
+    the launch configuration the benchmark times, checked on 1500 sampled cells."""
+    sp = [2 * math.pi / n for n in shape[::-1]]
+    dt = 0.8 * sp[0] / 2.0
+    phi = W.random_modes(shape, W.draw_modes(3, 32, 8, seed=0), device=DEV, dtype=torch.float32)
+    vel = W.abc_velocity(shape, device=DEV, dtype=torch.float32)
+    out = sl.advect(phi, vel, dt, sp, "CEC", parity)
+    cells = sample_cells(shape, 1500, seed=11 + parity)
+    ref = oracle_at_cells(phi, vel, sp, dt, "CEC", parity, cells)
+    got = out[cells[:, 2], cells[:, 1], cells[:, 0]].cpu().double().numpy()
+    assert rel_l2(got, ref) <= 1e-5
+
+
+def test_batched_equals_single_instance_steps():
+    sizes = [(64, 64, 64), (32, 96, 32), (40, 24, 48), (16, 16, 16)]
+    insts, keep, refs = [], [], []
+    for i, s in enumerate(sizes):
+        sp = [2 * math.pi / n for n in s[::-1]]
+        phi = W.random_modes(s, W.draw_modes(3, 8, 4, seed=i), device=DEV, dtype=torch.float32)
+        vel = W.abc_velocity(s, A=1.0 + 0.1 * i, device=DEV, dtype=torch.float32)
+        dt = 0.8 * min(sp) / 2.5
+        a, b = phi.clone(), torch.empty_like(phi)
+        keep.append((a, b, vel, sp, dt, phi))
+        insts.append(sl.Instance(a.data_ptr(), b.data_ptr(), vel.data_ptr(), (s[2], s[1], s[0]),
+                                 tuple(sp), dt))
+    h = sl.sl_batch_create(insts, tile_z=16)
+    try:
+        for k in range(3):
+            sl.sl_batch_step(h, k)
+        torch.cuda.synchronize()
+    finally:
+        sl.sl_batch_destroy(h)
+    for a, b, vel, sp, dt, phi in keep:
+        cur = phi
+        for k in range(3):
+            cur = sl.advect(cur, vel, dt, sp, "CEC", k)
+        result = b if 3 % 2 == 1 else a
+        assert torch.equal(result, cur)
+
+
+def test_autotune_keeps_results():
+    shape = (64, 64, 64)
+    phi, vel, sp, dt = random_case(shape, seed=12)
+    p, v = phi.to(DEV), vel.to(DEV)
+    before = sl.advect(p, v, dt, sp, "CEC", 0)
+    tz = sl.sl_autotune(torch.empty_like(p), p, v, 3, [64, 64, 64], sp, dt, sl.F32)
+    assert 1 <= tz <= 64
+    assert torch.equal(sl.advect(p, v, dt, sp, "CEC", 0), before)
