@@ -142,6 +142,32 @@ int sl_norms(const void *a, const void *b, int64_t n, int dtype, double out[3],
              void *stream);
 
 /*
+ * sl_norms for callers that cannot allocate device memory: the same FP64
+ * reduction, but its scratch is a fixed 32.8 KB array compiled into the
+ * library (resident on every GPU that loads it until the process exits), and
+ * the three results go to the caller's DEVICE buffer out (3 doubles, same order
+ * as sl_norms) asynchronously on the stream; nothing is copied to the host and
+ * the stream is not synchronised.  The paper has no counterpart: this is a
+ * library-interface variant.
+ *
+ * Who needs it: code that runs while a CUDA stream is being captured into a
+ * graph (cudaMalloc is not permitted there), applications whose device memory
+ * is handed out by their own pool and must see no driver allocation inside a
+ * time loop, and callbacks with a fixed memory budget.  sl_norms itself
+ * creates the library's device context with cudaMalloc on its first call and
+ * synchronises the stream, which those callers cannot accept.
+ *
+ * The first call on a device resolves the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ * n must be in [1, 2^40]; larger or smaller values return SL_ERR_ARG.  All calls
+ * share the one array: calls whose kernels overlap on the GPU (e.g. on two
+ * streams at once) race and may return wrong norms; serialise them.
+ */
+int sl_norms_static(const void *a, const void *b, int64_t n, int dtype, double *out,
+                    void *stream);
+
+/*
  * Read and clear the device status word of the current device (SL_DEV_*
  * bits).  Synchronises the stream first.
  */

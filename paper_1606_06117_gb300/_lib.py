@@ -29,7 +29,7 @@ STATUS = {0: "SL_OK", -1: "SL_ERR_ARG", -2: "SL_ERR_ALIAS", -3: "SL_ERR_CFL", -4
 #: every symbol include/sl.h declares
 EXPORTS = ("sl_version", "sl_last_error", "sl_init", "sl_advect", "sl_advect_multi", "sl_advect_host",
            "sl_release_host_staging", "sl_courant_max", "sl_norms", "sl_device_status", "sl_batch_create",
-           "sl_batch_step", "sl_batch_destroy", "sl_autotune")
+           "sl_batch_step", "sl_batch_destroy", "sl_autotune", "sl_norms_static")
 
 
 class SLError(RuntimeError):
@@ -74,6 +74,7 @@ def load(path: str | None = None):
             "sl_release_host_staging": ([], i),
             "sl_courant_max": ([vp, i, i64p, dp, d, i, dp, vp], i),
             "sl_norms": ([vp, vp, ctypes.c_int64, i, dp, vp], i),
+            "sl_norms_static": ([vp, vp, ctypes.c_int64, i, vp, vp], i),
             "sl_device_status": ([vp, ctypes.POINTER(ctypes.c_uint)], i),
             "sl_batch_create": ([ctypes.POINTER(vp), ctypes.POINTER(Instance), i, i, i, i], i),
             "sl_batch_step": ([vp, i, vp], i),
@@ -172,6 +173,11 @@ def sl_norms(a, b, n, dtype, stream=None):
     out = (ctypes.c_double * 3)()
     _check(load().sl_norms(_ptr(a), _ptr(b), int(n), int(dtype), out, _stream(stream)))
     return tuple(out)
+
+
+def sl_norms_static(a, b, n, dtype, out, stream=None):
+    """Norms into the device buffer ``out`` (3 float64) with no allocation."""
+    return _check(load().sl_norms_static(_ptr(a), _ptr(b), int(n), int(dtype), _ptr(out), _stream(stream)))
 
 
 def sl_device_status(stream=None):

@@ -99,6 +99,8 @@ int launch_step(void *out, const void *in, const void *vel, int ndim, const int6
 
 }  // namespace
 
+int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
 DevCtx *ctx_get()
 {
     int dev = 0;

@@ -60,4 +60,10 @@ cudaError_t launch_batched_cec(const BatchRec *dev_recs, int ninst, int nitems, 
 
 int default_tz(int dtype, int ndim, const int64_t dims[3]);
 
+// Records a thread-local error message (read by sl_last_error) and returns code.
+int set_error(int code, const char *msg);
+
+// Largest element count sl_norms_static accepts.
+constexpr int64_t kNormsStaticMaxElems = (int64_t)1 << 40;
+
 }  // namespace sl
