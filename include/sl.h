@@ -206,10 +206,14 @@ int sl_batch_step(sl_batch *b, int step_index, void *stream);
 int sl_batch_destroy(sl_batch *b);
 
 /*
- * Autotune: time the candidate z extents of the fused SL_CEC kernel for this
- * grid on the given stream (device buffers supplied by the caller; the step is
- * run several times, so out is overwritten) and cache the fastest for later
- * calls with the same (dims, dtype).  Returns the chosen tile_z in *tile_z.
+ * Autotune: time the candidate launch shapes of the fused SL_CEC kernel for
+ * this grid on the given stream (device buffers supplied by the caller; the
+ * step is run several times, so out is overwritten) and cache the fastest for
+ * later calls with the same (dims, dtype).  The candidates are z extents of a
+ * work item for the generic kernel, or CTA counts (one or two waves of CTAs
+ * per SM) for the persistent FP32 kernel used when dims[0] and dims[1] are
+ * multiples of 32 (dims[0] >= 64, dims[2] >= 8) and the buffers are 16-byte
+ * aligned.  The chosen value is returned in *tile_z.
  */
 int sl_autotune(void *out, const void *in, const void *vel, int ndim,
                 const int64_t dims[3], const double spacing[3], double dt,

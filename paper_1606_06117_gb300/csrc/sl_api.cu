@@ -29,8 +29,13 @@ struct Staging {
 };
 Staging g_stage[kMaxDev];
 
-// autotuned z chunk per (nx, ny, nz, dtype)
-std::map<std::tuple<int64_t, int64_t, int64_t, int>, int> g_tuned;
+// autotuned launch shape per (nx, ny, nz, dtype): z chunk of the generic
+// kernels and CTA count of the fast persistent CEC kernel
+struct Tuned {
+    int tz = 0;
+    int grid = 0;
+};
+std::map<std::tuple<int64_t, int64_t, int64_t, int>, Tuned> g_tuned;
 
 int fail(int code, const char *fmt, ...)
 {
@@ -86,13 +91,23 @@ int launch_step(void *out, const void *in, const void *vel, int ndim, const int6
 {
     Launch lc;
     lc.aligned = aligned16(out) && aligned16(in) && aligned16(vel);
+    Tuned tu;
     {
         std::lock_guard<std::mutex> lk(g_mu);
         auto it = g_tuned.find(std::make_tuple(dims[0], dims[1], dims[2], dtype));
-        if (it != g_tuned.end()) lc.tz = it->second;
+        if (it != g_tuned.end()) tu = it->second;
     }
-    cudaError_t e = scheme == SL_CEC ? launch_split_cec(dtype, in, out, vel, ndim, dims, s, parity, lc, c->status, st)
-                                     : launch_unsplit(dtype, scheme, in, out, vel, ndim, dims, s, lc, c->status, st);
+    cudaError_t e;
+    if (scheme == SL_CEC && fast_eligible(dims, ndim, dtype, lc.aligned)) {
+        FastInst one;
+        fast_fill(one, in, out, vel, dims, s, 0);
+        e = launch_cec_fast(one, nullptr, 1, (int64_t)one.ntiles * one.nz, parity, c->status, tu.grid, st);
+    } else if (scheme == SL_CEC) {
+        lc.tz = tu.tz;
+        e = launch_split_cec(dtype, in, out, vel, ndim, dims, s, parity, lc, c->status, st);
+    } else {
+        e = launch_unsplit(dtype, scheme, in, out, vel, ndim, dims, s, lc, c->status, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return SL_OK;
 }
@@ -132,8 +147,11 @@ struct sl_batch {
     int n = 0;
     int scheme = SL_CEC;
     int dtype = SL_F32;
-    BatchRec *dev_recs = nullptr;
-    unsigned *counter = nullptr;
+    bool fast = false;             // every instance takes the fast persistent path
+    BatchRec *dev_recs = nullptr;  // generic path: work-queue records
+    FastInst *dev_fast = nullptr;  // fast path: [2][n] tables (even: a -> b, odd: b -> a)
+    int64_t fast_total = 0;
+    unsigned *counter = nullptr;   // owns the device allocation
     int nitems[2] = {0, 0};
     int grid[2] = {0, 0};
 };
@@ -347,8 +365,21 @@ int sl_batch_create(sl_batch **out, const sl_instance *inst, int n, int scheme, 
             total[par] += g.tiles_x * g.tiles_y * g.chunks;
         }
     }
+    bool fast = true;
+    std::vector<FastInst> ftab(2 * (size_t)n);
+    int64_t ftotal = 0;
+    for (int i = 0; i < n; ++i) {
+        const sl_instance &in = inst[i];
+        double s[3] = {in.dt / in.spacing[0], in.dt / in.spacing[1], in.dt / in.spacing[2]};
+        if (!fast_eligible(in.dims, 3, dtype, true)) fast = false;
+        fast_fill(ftab[i], in.a, in.b, in.vel, in.dims, s, ftotal);
+        fast_fill(ftab[n + i], in.b, in.a, in.vel, in.dims, s, ftotal);
+        ftotal += (int64_t)ftab[i].ntiles * ftab[i].nz;
+    }
     sl_batch *b = new (std::nothrow) sl_batch();
     if (!b) return fail(SL_ERR_NOMEM, "host allocation");
+    b->fast = fast;
+    b->fast_total = ftotal;
     b->device = c->device;
     b->n = n;
     b->scheme = scheme;
@@ -357,13 +388,17 @@ int sl_batch_create(sl_batch **out, const sl_instance *inst, int n, int scheme, 
     b->nitems[1] = total[1];
     for (int par = 0; par < 2; ++par) b->grid[par] = std::min(total[par], c->num_sms * batched_blocks_per_sm(par));
     void *p = nullptr;
-    if (cudaMalloc(&p, sizeof(BatchRec) * n + 256) != cudaSuccess) {
+    const size_t rec_bytes = (sizeof(BatchRec) * n + 255) & ~(size_t)255;
+    if (cudaMalloc(&p, 256 + rec_bytes + sizeof(FastInst) * 2 * n) != cudaSuccess) {
         delete b;
         return fail(SL_ERR_NOMEM, "device instance table");
     }
     b->counter = static_cast<unsigned *>(p);
     b->dev_recs = reinterpret_cast<BatchRec *>(static_cast<char *>(p) + 256);
+    b->dev_fast = reinterpret_cast<FastInst *>(static_cast<char *>(p) + 256 + rec_bytes);
     cudaError_t e = cudaMemcpy(b->dev_recs, recs.data(), sizeof(BatchRec) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->dev_fast, ftab.data(), sizeof(FastInst) * 2 * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->counter, 0, 256);
     if (e != cudaSuccess) {
         cudaFree(p);
@@ -382,9 +417,15 @@ int sl_batch_step(sl_batch *b, int step_index, void *stream)
     if (c->device != b->device) return fail(SL_ERR_ARG, "batch belongs to device %d", b->device);
     const int par = step_index & 1;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(unsigned), st);
-    if (e == cudaSuccess)
-        e = launch_batched_cec(b->dev_recs, b->n, b->nitems[par], par, b->counter, c->status, b->grid[par], st);
+    cudaError_t e;
+    if (b->fast) {
+        FastInst dummy{};
+        e = launch_cec_fast(dummy, b->dev_fast + (size_t)par * b->n, b->n, b->fast_total, par, c->status, 0, st);
+    } else {
+        e = cudaMemsetAsync(b->counter, 0, sizeof(unsigned), st);
+        if (e == cudaSuccess)
+            e = launch_batched_cec(b->dev_recs, b->n, b->nitems[par], par, b->counter, c->status, b->grid[par], st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "batched launch");
     return SL_OK;
 }
@@ -413,24 +454,37 @@ int sl_autotune(void *out, const void *in, const void *vel, int ndim, const int6
         *tile_z = 1;
         return SL_OK;
     }
+    const bool fast = fast_eligible(dims, ndim, dtype, aligned16(out) && aligned16(in) && aligned16(vel));
     std::vector<int> cands;
-    for (int tz : {8, 16, 24, 32, 48, 64, 96, 128, 192, 256})
-        if (tz <= dims[2]) cands.push_back(tz);
-    if (cands.empty() || cands.back() != (int)dims[2]) cands.push_back((int)dims[2]);
+    if (fast) {
+        // CTA counts of the persistent kernel: whole waves of 1 or 2 CTAs per SM
+        const int g1 = fast_grid(0) / 2 > 0 ? fast_grid(0) / 2 : c->num_sms;
+        for (int g : {g1, 2 * g1}) cands.push_back(g);
+    } else {
+        for (int tz : {8, 16, 24, 32, 48, 64, 96, 128, 192, 256})
+            if (tz <= dims[2]) cands.push_back(tz);
+        if (cands.empty() || cands.back() != (int)dims[2]) cands.push_back((int)dims[2]);
+    }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(SL_ERR_CUDA, "events");
     float best = 1e30f;
     int best_tz = cands.front();
     Launch lc;
     lc.aligned = aligned16(out) && aligned16(in) && aligned16(vel);
-    for (int tz : cands) {
-        lc.tz = tz;
+    FastInst one;
+    fast_fill(one, in, out, vel, dims, s, 0);
+    auto run = [&](int cand, int rep) {
+        if (fast) return launch_cec_fast(one, nullptr, 1, (int64_t)one.ntiles * one.nz, rep, c->status, cand, st);
+        lc.tz = cand;
+        return launch_split_cec(dtype, in, out, vel, ndim, dims, s, rep, lc, c->status, st);
+    };
+    for (int cand : cands) {
         float tot = 0.0f;
         cudaError_t e = cudaSuccess;
         for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
-            e = launch_split_cec(dtype, in, out, vel, ndim, dims, s, rep, lc, c->status, st);   // warm-up
+            e = run(cand, rep);   // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-            if (e == cudaSuccess) e = launch_split_cec(dtype, in, out, vel, ndim, dims, s, rep, lc, c->status, st);
+            if (e == cudaSuccess) e = run(cand, rep);
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.0f;
@@ -444,14 +498,15 @@ int sl_autotune(void *out, const void *in, const void *vel, int ndim, const int6
         }
         if (tot < best) {
             best = tot;
-            best_tz = tz;
+            best_tz = cand;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        g_tuned[std::make_tuple(dims[0], dims[1], dims[2], dtype)] = best_tz;
+        Tuned &t = g_tuned[std::make_tuple(dims[0], dims[1], dims[2], dtype)];
+        if (fast) t.grid = best_tz; else t.tz = best_tz;
     }
     *tile_z = best_tz;
     return SL_OK;

@@ -60,6 +60,25 @@ cudaError_t launch_batched_cec(const BatchRec *dev_recs, int ninst, int nitems, 
 
 int default_tz(int dtype, int ndim, const int64_t dims[3]);
 
+// Fast FP32 CEC path (k_cec_fast.cu): one periodic grid of whole 32 x 32 column
+// tiles; w0 numbers its first (column tile, plane) pair in a batch.
+struct FastInst {
+    const float *in;
+    float *out;
+    const float *vel;
+    int nx, ny, nz;
+    int tiles_x, ntiles;
+    int64_t plane, ncell;
+    float sx, sy, sz;
+    int64_t w0;
+};
+bool fast_eligible(const int64_t dims[3], int ndim, int dtype, bool aligned);
+void fast_fill(FastInst &f, const void *in, void *out, const void *vel, const int64_t dims[3], const double s[3],
+               int64_t w0);
+cudaError_t launch_cec_fast(const FastInst &one, const FastInst *dev_table, int ninst, int64_t total, int parity,
+                            unsigned *status, int grid_req, cudaStream_t st);
+int fast_grid(int parity);
+
 // Records a thread-local error message (read by sl_last_error) and returns code.
 int set_error(int code, const char *msg);
 
