@@ -21,7 +21,7 @@
 namespace sl {
 namespace {
 
-constexpr unsigned kWaitLimit = 1u << 22;   // mbarrier polls before giving up
+constexpr unsigned kWaitLimit = 1u << 20;   // mbarrier polls before giving up
 
 // ---------------------------------------------------------------- mbarrier
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
