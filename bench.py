@@ -76,7 +76,7 @@ def measured_hbm_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("k_split.cu", "sl_common.cuh"):
+    for f in ("k_cec_fast.cu", "sl_common.cuh"):
         with open(os.path.join(ROOT, "paper_1606_06117_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -85,7 +85,7 @@ def kernel_source_hash():
 def profiled_traffic(workload):
     """DRAM bytes per launch of the CEC kernel from the committed ncu summary, or
     None when the summary is missing or was taken on other kernel sources."""
-    p = os.path.join(ROOT, "profiles", f"k_cec_xyz_{workload}.md")
+    p = os.path.join(ROOT, "profiles", f"k_cec_fast_{workload}.md")
     try:
         text = open(p).read()
     except OSError:
@@ -319,7 +319,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{world}"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                             "kernel": "k_cec_xyz / k_cec_zyx (alternating)",
+                             "kernel": "k_cec_xyz_fast / k_cec_zyx_fast (alternating)",
                              "bytes_per_launch": BYTES_PER_CELL * ncell},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk,
                 "device_status": sl_status}

@@ -147,25 +147,35 @@ struct Seg {
 };
 
 // Walks a CTA's share [w, wend) of the numbered (column tile, plane) pairs.
+// The pairs of one column tile are numbered from a tile-dependent plane phi
+// (periodic in z), chosen so that the share boundaries of every tile fall on
+// the same planes: CTAs that start together then process the same z plane of
+// neighbouring tiles at about the same time, and the halo rows one tile stages
+// are still in L2 when its neighbours stage them.
 __device__ __forceinline__ bool next_seg(const FastInst *tab, int ninst, int64_t &w, int64_t wend, int &hint,
-                                         Seg &s)
+                                         double share, Seg &s)
 {
     if (w >= wend) return false;
     while (hint + 1 < ninst && tab[hint + 1].w0 <= w) ++hint;
     const FastInst &I = tab[hint];
     const int64_t local = w - I.w0;
     const int t = (int)(local / I.nz);
-    const int z = (int)(local - (int64_t)t * I.nz);
-    const int64_t tile_end = I.w0 + (int64_t)(t + 1) * I.nz;
+    const int o = (int)(local - (int64_t)t * I.nz);
+    const int64_t tile_w = I.w0 + (int64_t)t * I.nz;
+    int phi = (int)(fmod((double)tile_w, share) + 0.5);
+    phi = phi % I.nz;
+    const int64_t tile_end = tile_w + I.nz;
     const int64_t e = wend < tile_end ? wend : tile_end;
     s.inst = hint;
     s.tx = t % I.tiles_x;
     s.ty = t / I.tiles_x;
-    s.z0 = z;
-    s.z1 = z + (int)(e - w);
+    s.z0 = o + phi;                    // in [0, 2 nz); planes are taken modulo nz
+    s.z1 = s.z0 + (int)(e - w);
     w = e;
     return true;
 }
+
+__device__ __forceinline__ int wrapz(int p, int nz) { return ((p % nz) + nz) % nz; }
 
 // Row copies of one staged array: rows [r0, r0 + nr) relative to the tile, x
 // range [x0 + c0, x0 + c0 + w) split at the periodic seam (at most one split,
@@ -234,7 +244,7 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
     Seg sg;
     const int cx = tid % TX, yr = (tid / TX) * RY;
 
-    while (next_seg(tab, ninst, w, wend, hint, sg)) {
+    while (next_seg(tab, ninst, w, wend, hint, (double)total / (double)G, sg)) {
         const FastInst &I = tab[sg.inst];
         const int x0 = sg.tx * TX, y0 = sg.ty * TY;
         const float sx = I.sx, sy = I.sy, sz = I.sz;
@@ -248,7 +258,7 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
                     mbar_expect_tx(&bar[slot], BYTES);
                 }
                 __syncwarp();
-                const int pz = p < 0 ? p + I.nz : (p >= I.nz ? p - I.nz : p);
+                const int pz = wrapz(p, I.nz);
                 const int pz1 = pz == 0 ? I.nz - 1 : pz - 1;
                 const float *pl = I.in + (int64_t)pz * I.plane;
                 const float *vx = I.vel + (int64_t)pz * I.plane;
@@ -315,7 +325,7 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
             cec_run<RY>(pv, cv, o);
             const int kz = p - 3;
             const bool store = kz >= sg.z0;
-            float *dst = I.out + (int64_t)(kz < 0 ? kz + I.nz : kz) * I.plane + (int64_t)(y0 + yr) * I.nx + x0 + cx;
+            float *dst = I.out + (int64_t)wrapz(kz, I.nz) * I.plane + (int64_t)(y0 + yr) * I.nx + x0 + cx;
 #pragma unroll
             for (int i = 0; i < RY; ++i) {
                 const float c = czP[(yr + i) * TX + cx] * sz;
@@ -396,7 +406,7 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
         zoff[j] = r < NZC ? (r / (TX + 6)) * PW + (r % (TX + 6)) + 1 : -1;
     }
 
-    while (next_seg(tab, ninst, w, wend, hint, sg)) {
+    while (next_seg(tab, ninst, w, wend, hint, (double)total / (double)G, sg)) {
         const FastInst &I = tab[sg.inst];
         const int x0 = sg.tx * TX, y0 = sg.ty * TY;
         const float sx = I.sx, sy = I.sy, sz = I.sz;
@@ -411,10 +421,9 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
                 }
                 __syncwarp();
                 const int nz = I.nz;
-                const int pz = p < 0 ? p + nz : (p >= nz ? p - nz : p);
+                const int pz = wrapz(p, nz);
                 const int pz1 = pz == 0 ? nz - 1 : pz - 1;
-                int pk = p - 3;
-                pk = pk < 0 ? pk + nz : (pk >= nz ? pk - nz : pk);
+                const int pk = wrapz(p - 3, nz);
                 const float *vk = I.vel + (int64_t)pk * I.plane;
                 stage_array(lane, sb, PW, I.in + (int64_t)pz * I.plane, I.nx, I.ny, x0, y0, -3, PH, -4, TX + 8,
                             &bar[slot]);
@@ -496,8 +505,8 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
 #pragma unroll
                 for (int k = 2; k < RX + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
                 cec_run<RX>(pv, cv, o);
-                float4 *dst = reinterpret_cast<float4 *>(I.out + (int64_t)kz * I.plane + (int64_t)(y0 + row) * I.nx +
-                                                         x0 + xr);
+                float4 *dst = reinterpret_cast<float4 *>(I.out + (int64_t)wrapz(kz, I.nz) * I.plane +
+                                                         (int64_t)(y0 + row) * I.nx + x0 + xr);
                 dst[0] = make_float4(o[0], o[1], o[2], o[3]);
                 dst[1] = make_float4(o[4], o[5], o[6], o[7]);
             }
