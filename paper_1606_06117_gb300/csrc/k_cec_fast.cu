@@ -5,9 +5,8 @@
 // Sec. 5 eqs. split:1-2), organised for instruction economy:
 //
 //  - Staging: each x-y plane of Phi and u (with its periodic halo) is copied
-//    row by row with cp.async.bulk by one warp; the other warps only compute.
-//    Completion is tracked by one mbarrier per buffer slot (transaction bytes);
-//    every wait is bounded and reports SL_DEV_TIMEOUT instead of hanging.
+//    in 16-byte cp.async chunks whose source and destination offsets every
+//    thread computes once per segment, double-buffered one plane ahead.
 //  - Work split: persistent CTAs; the (column tile, plane) pairs of all grids
 //    are numbered and every CTA takes one contiguous, equal share, walking
 //    z inside each column tile, so every SM gets the same number of planes.
@@ -20,54 +19,6 @@
 
 namespace sl {
 namespace {
-
-constexpr unsigned kWaitLimit = 1u << 20;   // mbarrier polls before giving up
-
-// ---------------------------------------------------------------- mbarrier
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait; returns false if the phase did not complete in time.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
-{
-    for (unsigned it = 0; it < kWaitLimit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
 
 // ------------------------------------------------------------ 1D sweep math
 // cec_run: outputs o[0..R) of a line from p[0..R+6) = Phi at offsets -3..R+2
@@ -177,30 +128,45 @@ __device__ __forceinline__ bool next_seg(const FastInst *tab, int ninst, int64_t
 
 __device__ __forceinline__ int wrapz(int p, int nz) { return ((p % nz) + nz) % nz; }
 
-// Row copies of one staged array: rows [r0, r0 + nr) relative to the tile, x
-// range [x0 + c0, x0 + c0 + w) split at the periodic seam (at most one split,
-// since nx >= w).  Issued by the lanes of one warp.
-__device__ __forceinline__ void stage_array(int lane, float *dst, int ld, const float *plane, int nx, int ny,
-                                            int x0, int y0, int r0, int nr, int c0, int w, uint64_t *bar)
-{
-    int xa = x0 + c0;
-    int s1 = 0, n1 = w, s2 = 0, n2 = 0, o2 = 0;      // first piece [s1, s1+n1), second [s2, s2+n2) at dst o2
-    if (xa < 0) {
-        s1 = xa + nx; n1 = -xa; s2 = 0; n2 = w + xa; o2 = -xa;
-    } else if (xa + w > nx) {
-        s1 = xa; n1 = nx - xa; s2 = 0; n2 = xa + w - nx; o2 = nx - xa;
-    } else {
-        s1 = xa;
+// 16-byte chunks of one staged array: rows [r0, r0 + NR) relative to the
+// tile, x range [x0 + c0, x0 + c0 + 4 CPR) (c0 and x0 multiples of 4, nx a
+// multiple of 4, so no chunk straddles the periodic seam).  Thread tid owns
+// chunks tid + k NT; the in-plane source offset and the shared-memory offset
+// of each are computed once per segment.
+template <int NT, int NR, int CPR, int LD>
+struct Chunks {
+    static constexpr int N = NR * CPR;
+    static constexpr int K = (N + NT - 1) / NT;
+    int src[K];
+    int dst[K];
+
+    __device__ __forceinline__ void setup(int tid, int x0, int y0, int r0, int c0, int nx, int ny)
+    {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int idx = tid + k * NT;
+            if (idx < N) {
+                const int row = idx / CPR, cc = idx - (idx / CPR) * CPR;
+                int gy = y0 + r0 + row;
+                gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+                int gx = x0 + c0 + 4 * cc;
+                gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+                src[k] = gy * nx + gx;
+                dst[k] = row * LD + 4 * cc;
+            } else {
+                src[k] = -1;
+                dst[k] = 0;
+            }
+        }
     }
-    for (int r = lane; r < nr; r += 32) {
-        int gy = y0 + r0 + r;
-        gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
-        const float *src = plane + (int64_t)gy * nx;
-        float *d = dst + r * ld;
-        bulk_g2s(d, src + s1, 4u * n1, bar);
-        if (n2) bulk_g2s(d + o2, src + s2, 4u * n2, bar);
+
+    __device__ __forceinline__ void issue(float *sdst, const float *gsrc) const
+    {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (src[k] >= 0) cp_async16(sdst + dst[k], gsrc + src[k]);
     }
-}
+};
 
 // ============================================================ order x, y, z
 namespace xyz {
@@ -211,8 +177,7 @@ constexpr int SZ_CY = (TY + 4) * TX;                  // u_y rows [-2, TY+2), x 
 constexpr int SZ_CZ = TY * TX;                        // u_z rows [0, TY)
 constexpr int SLOT = 2 * SZ_PHI + SZ_CY + SZ_CZ;
 constexpr int SZ_S1 = PH * TX;                        // x-swept rows
-constexpr unsigned BYTES = 4u * (2 * PH * (TX + 8) + (TY + 4) * TX + TY * TX);
-constexpr size_t SMEM = sizeof(float) * (2 * SLOT + SZ_S1) + 64 + 128;
+constexpr size_t SMEM = sizeof(float) * (2 * SLOT + SZ_S1) + 128;
 }  // namespace xyz
 
 template <bool BATCH>
@@ -223,26 +188,19 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *buf = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float *sS1 = buf + 2 * SLOT;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sS1 + SZ_S1);
-    __shared__ int s_abort;
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
     const FastInst *tab = BATCH ? table : &one;
     const int64_t G = gridDim.x;
     int64_t w = total * blockIdx.x / G;
     const int64_t wend = total * (blockIdx.x + 1) / G;
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-        s_abort = 0;
-    }
-    __syncthreads();
-    unsigned uses[2] = {0u, 0u};
     bool bad = false;
     int hint = 0;
     Seg sg;
     const int cx = tid % TX, yr = (tid / TX) * RY;
+    Chunks<NT, PH, (TX + 8) / 4, PW> chPhi;        // Phi and u_x: rows [-3, TY+3), x [-4, TX+4)
+    Chunks<NT, TY + 4, TX / 4, TX> chCy;           // u_y: rows [-2, TY+2), x [0, TX)
+    Chunks<NT, TY, TX / 4, TX> chCz;               // u_z: rows [0, TY)
 
     while (next_seg(tab, ninst, w, wend, hint, (double)total / (double)G, sg)) {
         const FastInst &I = tab[sg.inst];
@@ -250,25 +208,19 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
         const float sx = I.sx, sy = I.sy, sz = I.sz;
         const int pfirst = sg.z0 - 3, plast = sg.z1 + 2;
 
+        chPhi.setup(tid, x0, y0, -3, -4, I.nx, I.ny);
+        chCy.setup(tid, x0, y0, -2, 0, I.nx, I.ny);
+        chCz.setup(tid, x0, y0, 0, 0, I.nx, I.ny);
         auto issue = [&](int p, int slot) {
-            if (warp == 0) {
-                float *sb = buf + slot * SLOT;
-                if (lane == 0) {
-                    fence_proxy_async();
-                    mbar_expect_tx(&bar[slot], BYTES);
-                }
-                __syncwarp();
-                const int pz = wrapz(p, I.nz);
-                const int pz1 = pz == 0 ? I.nz - 1 : pz - 1;
-                const float *pl = I.in + (int64_t)pz * I.plane;
-                const float *vx = I.vel + (int64_t)pz * I.plane;
-                stage_array(lane, sb, PW, pl, I.nx, I.ny, x0, y0, -3, PH, -4, TX + 8, &bar[slot]);
-                stage_array(lane, sb + SZ_PHI, PW, vx, I.nx, I.ny, x0, y0, -3, PH, -4, TX + 8, &bar[slot]);
-                stage_array(lane, sb + 2 * SZ_PHI, TX, vx + I.ncell, I.nx, I.ny, x0, y0, -2, TY + 4, 0, TX,
-                            &bar[slot]);
-                stage_array(lane, sb + 2 * SZ_PHI + SZ_CY, TX, I.vel + 2 * I.ncell + (int64_t)pz1 * I.plane, I.nx,
-                            I.ny, x0, y0, 0, TY, 0, TX, &bar[slot]);
-            }
+            float *sb = buf + slot * SLOT;
+            const int pz = wrapz(p, I.nz);
+            const int pz1 = pz == 0 ? I.nz - 1 : pz - 1;
+            const float *vx = I.vel + (int64_t)pz * I.plane;
+            chPhi.issue(sb, I.in + (int64_t)pz * I.plane);
+            chPhi.issue(sb + SZ_PHI, vx);
+            chCy.issue(sb + 2 * SZ_PHI, vx + I.ncell);
+            chCz.issue(sb + 2 * SZ_PHI + SZ_CY, I.vel + 2 * I.ncell + (int64_t)pz1 * I.plane);
+            cp_async_commit();
         };
 
         ZCol win[RY];
@@ -279,11 +231,8 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
         auto plane = [&](auto PC, int p) {
             constexpr int P = decltype(PC)::value;
             const int slot = (p - pfirst) & 1;
-            const bool ok = mbar_wait(&bar[slot], uses[slot] & 1u);
-            uses[slot]++;
-            if (!ok) s_abort = 1;
+            cp_async_wait_all();
             __syncthreads();
-            if (s_abort) return false;
             if (p < plast) issue(p + 1, slot ^ 1);
             const float *sb = buf + slot * SLOT;
             const float *phiP = sb, *cxP = sb + SZ_PHI, *cyP = sb + 2 * SZ_PHI, *czP = sb + 2 * SZ_PHI + SZ_CY;
@@ -333,31 +282,21 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
                 const float v = win[i].push<P>(o[i], c);
                 if (store) dst[(int64_t)i * I.nx] = v;
             }
-            return true;
         };
 
         issue(pfirst, 0);
-        bool alive = true;
-        for (int p = pfirst; p <= plast && alive; p += 2) {
-            alive = plane(std::integral_constant<int, 0>(), p);
-            if (alive && p + 1 <= plast) alive = plane(std::integral_constant<int, 1>(), p + 1);
+        for (int p = pfirst; p <= plast; p += 2) {
+            plane(std::integral_constant<int, 0>(), p);
+            if (p + 1 <= plast) plane(std::integral_constant<int, 1>(), p + 1);
         }
-        // both slots were consumed as often as they were filled
-        __syncthreads();
-        if (!alive) break;
-    }
-    if (s_abort && tid == 0) {
-        atomicOr(status, 2u);
-        // give copies still in flight a bounded time to land before the CTA exits
-        mbar_wait(&bar[0], uses[0] & 1u);
-        mbar_wait(&bar[1], uses[1] & 1u);
+        __syncthreads();   // shared buffers are reused by the next segment
     }
     flag_cfl(status, bad);
 }
 
 // ============================================================ order z, y, x
 namespace zyx {
-constexpr int TX = 32, TY = 32, NT = 256, RX = 8, RY = 8;
+constexpr int TX = 32, TY = 32, NT = 512, RX = 8, RY = 8;
 constexpr int PH = TY + 6, PW = TX + 12;
 constexpr int SZ_PHI = PH * PW;                      // Phi and u_z (plane p-1): rows [-3, TY+3)
 constexpr int SZ_CY = (TY + 4) * PW;                 // u_y (plane p-3): rows [-2, TY+2)
@@ -365,40 +304,33 @@ constexpr int SZ_CX = TY * PW;                       // u_x (plane p-3): rows [0
 constexpr int SLOT = 2 * SZ_PHI + SZ_CY + SZ_CX;
 constexpr int NZC = (TX + 6) * (TY + 6);             // z-swept columns (x, y in [-3, T+3))
 constexpr int NCOL = (NZC + NT - 1) / NT;
-constexpr unsigned BYTES = 4u * (TX + 8) * (2 * PH + (TY + 4) + TY);
-constexpr size_t SMEM = sizeof(float) * (2 * SLOT + SZ_PHI + SZ_CX) + 64 + 128;
+constexpr size_t SMEM = sizeof(float) * (2 * SLOT + SZ_PHI + SZ_CX) + 128;
 }  // namespace zyx
 
 template <bool BATCH>
-__global__ void __launch_bounds__(zyx::NT, 2)
-k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict__ table, int ninst, int64_t total, unsigned *status)
+__global__ void __launch_bounds__(zyx::NT, 1)
+k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict__ table, int ninst, int64_t total,
+               unsigned *status)
 {
     using namespace zyx;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *buf = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float *sZ = buf + 2 * SLOT;                      // z-swept plane, rows [-3, TY+3)
     float *sS2 = sZ + SZ_PHI;                        // y-swept rows [0, TY)
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sS2 + SZ_CX);
-    __shared__ int s_abort;
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
     const FastInst *tab = BATCH ? table : &one;
     const int64_t G = gridDim.x;
     int64_t w = total * blockIdx.x / G;
     const int64_t wend = total * (blockIdx.x + 1) / G;
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-        s_abort = 0;
-    }
-    __syncthreads();
-    unsigned uses[2] = {0u, 0u};
     bool bad = false;
     int hint = 0;
     Seg sg;
+    Chunks<NT, PH, (TX + 8) / 4, PW> chPhi;        // Phi and u_z: rows [-3, TY+3), x [-4, TX+4)
+    Chunks<NT, TY + 4, (TX + 8) / 4, PW> chCy;     // u_y: rows [-2, TY+2)
+    Chunks<NT, TY, (TX + 8) / 4, PW> chCx;         // u_x: rows [0, TY)
 
-    // per-thread z columns: staged (row, col) offsets, col = x + 4, row = y + 3
+    // per-thread z columns: staged offsets (row = y + 3, col = x + 4)
     int zoff[NCOL];
 #pragma unroll
     for (int j = 0; j < NCOL; ++j) {
@@ -411,28 +343,21 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
         const int x0 = sg.tx * TX, y0 = sg.ty * TY;
         const float sx = I.sx, sy = I.sy, sz = I.sz;
         const int pfirst = sg.z0 - 3, plast = sg.z1 + 2;
+        chPhi.setup(tid, x0, y0, -3, -4, I.nx, I.ny);
+        chCy.setup(tid, x0, y0, -2, -4, I.nx, I.ny);
+        chCx.setup(tid, x0, y0, 0, -4, I.nx, I.ny);
 
         auto issue = [&](int p, int slot) {
-            if (warp == 0) {
-                float *sb = buf + slot * SLOT;
-                if (lane == 0) {
-                    fence_proxy_async();
-                    mbar_expect_tx(&bar[slot], BYTES);
-                }
-                __syncwarp();
-                const int nz = I.nz;
-                const int pz = wrapz(p, nz);
-                const int pz1 = pz == 0 ? nz - 1 : pz - 1;
-                const int pk = wrapz(p - 3, nz);
-                const float *vk = I.vel + (int64_t)pk * I.plane;
-                stage_array(lane, sb, PW, I.in + (int64_t)pz * I.plane, I.nx, I.ny, x0, y0, -3, PH, -4, TX + 8,
-                            &bar[slot]);
-                stage_array(lane, sb + SZ_PHI, PW, I.vel + 2 * I.ncell + (int64_t)pz1 * I.plane, I.nx, I.ny, x0, y0,
-                            -3, PH, -4, TX + 8, &bar[slot]);
-                stage_array(lane, sb + 2 * SZ_PHI, PW, vk + I.ncell, I.nx, I.ny, x0, y0, -2, TY + 4, -4, TX + 8,
-                            &bar[slot]);
-                stage_array(lane, sb + 2 * SZ_PHI + SZ_CY, PW, vk, I.nx, I.ny, x0, y0, 0, TY, -4, TX + 8, &bar[slot]);
-            }
+            float *sb = buf + slot * SLOT;
+            const int nz = I.nz;
+            const int pz = wrapz(p, nz);
+            const int pz1 = pz == 0 ? nz - 1 : pz - 1;
+            const float *vk = I.vel + (int64_t)wrapz(p - 3, nz) * I.plane;
+            chPhi.issue(sb, I.in + (int64_t)pz * I.plane);
+            chPhi.issue(sb + SZ_PHI, I.vel + 2 * I.ncell + (int64_t)pz1 * I.plane);
+            chCy.issue(sb + 2 * SZ_PHI, vk + I.ncell);
+            chCx.issue(sb + 2 * SZ_PHI + SZ_CY, vk);
+            cp_async_commit();
         };
 
         ZCol win[NCOL];
@@ -442,11 +367,8 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
         auto plane = [&](auto PC, int p) {
             constexpr int P = decltype(PC)::value;
             const int slot = (p - pfirst) & 1;
-            const bool ok = mbar_wait(&bar[slot], uses[slot] & 1u);
-            uses[slot]++;
-            if (!ok) s_abort = 1;
+            cp_async_wait_all();
             __syncthreads();
-            if (s_abort) return false;
             if (p < plast) issue(p + 1, slot ^ 1);
             const float *sb = buf + slot * SLOT;
             const float *phiP = sb, *czP = sb + SZ_PHI, *cyP = sb + 2 * SZ_PHI, *cxP = sb + 2 * SZ_PHI + SZ_CY;
@@ -463,7 +385,7 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
             }
             __syncthreads();
             const int kz = p - 3;
-            if (kz < sg.z0) return true;
+            if (kz < sg.z0) return;
             // ---- y sweep: columns x in [-3, TX+3), rows [0, TY) -> sS2
             for (int r = tid; r < (TX + 6) * (TY / RY); r += NT) {
                 const int col = r % (TX + 6) + 1, yr = (r / (TX + 6)) * RY;
@@ -510,22 +432,14 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
                 dst[0] = make_float4(o[0], o[1], o[2], o[3]);
                 dst[1] = make_float4(o[4], o[5], o[6], o[7]);
             }
-            return true;
         };
 
         issue(pfirst, 0);
-        bool alive = true;
-        for (int p = pfirst; p <= plast && alive; p += 2) {
-            alive = plane(std::integral_constant<int, 0>(), p);
-            if (alive && p + 1 <= plast) alive = plane(std::integral_constant<int, 1>(), p + 1);
+        for (int p = pfirst; p <= plast; p += 2) {
+            plane(std::integral_constant<int, 0>(), p);
+            if (p + 1 <= plast) plane(std::integral_constant<int, 1>(), p + 1);
         }
         __syncthreads();
-        if (!alive) break;
-    }
-    if (s_abort && tid == 0) {
-        atomicOr(status, 2u);
-        mbar_wait(&bar[0], uses[0] & 1u);
-        mbar_wait(&bar[1], uses[1] & 1u);
     }
     flag_cfl(status, bad);
 }
