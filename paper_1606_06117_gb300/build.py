@@ -51,8 +51,8 @@ def _stamp(src: str, extra: list[str]) -> str:
     return h.hexdigest()[:16]
 
 
-def _compile(src: str, extra: list[str], verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+def _compile(src: str, extra: list[str], verbose: bool, outdir: str = BUILD) -> str:
+    obj = os.path.join(outdir, os.path.basename(src).replace(".cu", ".o"))
     stamp = obj + ".stamp"
     want = _stamp(src, extra)
     if os.path.exists(obj) and os.path.exists(stamp) and open(stamp).read() == want:
@@ -70,21 +70,26 @@ def _compile(src: str, extra: list[str], verbose: bool) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra: list[str] | None = None, jobs: int | None = None) -> str:
-    """Compile every csrc/*.cu for sm_103a and link libsl.so; returns its path."""
+def build(verbose: bool = False, extra: list[str] | None = None, jobs: int | None = None,
+          outdir: str | None = None) -> str:
+    """Compile every csrc/*.cu for sm_103a and link libsl.so; returns its path.
+    ``extra`` adds nvcc flags (e.g. -D tuning constants); ``outdir`` builds a
+    separate copy of the library there instead of _build/."""
     extra = list(extra or [])
-    os.makedirs(BUILD, exist_ok=True)
+    outdir = outdir or BUILD
+    lib = os.path.join(outdir, "libsl.so")
+    os.makedirs(outdir, exist_ok=True)
     srcs = _sources()
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra, verbose), srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, extra, verbose, outdir), srcs))
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

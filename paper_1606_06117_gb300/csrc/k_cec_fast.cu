@@ -169,6 +169,16 @@ struct Chunks {
 };
 
 // ============================================================ order x, y, z
+#ifndef SL_XYZ_MINB
+#define SL_XYZ_MINB 2      // CTAs per SM the x,y,z kernel is compiled for
+#endif
+#ifndef SL_ZYX_NT
+#define SL_ZYX_NT 512      // threads of the z,y,x kernel
+#endif
+#ifndef SL_ZYX_RY
+#define SL_ZYX_RY 8        // y-sweep run length of the z,y,x kernel
+#endif
+
 namespace xyz {
 constexpr int TX = 32, TY = 32, NT = 256, RX = 8, RY = 4;
 constexpr int PH = TY + 6, PW = TX + 12;              // Phi / u_x rows [-3, TY+3), x [-4, TX+4), stride 44
@@ -181,7 +191,7 @@ constexpr size_t SMEM = sizeof(float) * (2 * SLOT + SZ_S1) + 128;
 }  // namespace xyz
 
 template <bool BATCH>
-__global__ void __launch_bounds__(xyz::NT, 2)
+__global__ void __launch_bounds__(xyz::NT, SL_XYZ_MINB)
 k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict__ table, int ninst, int64_t total, unsigned *status)
 {
     using namespace xyz;
@@ -211,9 +221,9 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
         chPhi.setup(tid, x0, y0, -3, -4, I.nx, I.ny);
         chCy.setup(tid, x0, y0, -2, 0, I.nx, I.ny);
         chCz.setup(tid, x0, y0, 0, 0, I.nx, I.ny);
-        auto issue = [&](int p, int slot) {
+        // pz: plane index of the bundle, already reduced modulo nz
+        auto issue = [&](int pz, int slot) {
             float *sb = buf + slot * SLOT;
-            const int pz = wrapz(p, I.nz);
             const int pz1 = pz == 0 ? I.nz - 1 : pz - 1;
             const float *vx = I.vel + (int64_t)pz * I.plane;
             chPhi.issue(sb, I.in + (int64_t)pz * I.plane);
@@ -228,12 +238,13 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
         for (int i = 0; i < RY; ++i) win[i].init();
 
         // one plane: x sweep into sS1, y sweep, z windows, store
-        auto plane = [&](auto PC, int p) {
+        // p: unreduced plane; zw: p modulo nz
+        auto plane = [&](auto PC, int p, int zw) {
             constexpr int P = decltype(PC)::value;
             const int slot = (p - pfirst) & 1;
             cp_async_wait_all();
             __syncthreads();
-            if (p < plast) issue(p + 1, slot ^ 1);
+            if (p < plast) issue(zw + 1 == I.nz ? 0 : zw + 1, slot ^ 1);
             const float *sb = buf + slot * SLOT;
             const float *phiP = sb, *cxP = sb + SZ_PHI, *cyP = sb + 2 * SZ_PHI, *czP = sb + 2 * SZ_PHI + SZ_CY;
             constexpr int XR = TX / RX;
@@ -272,9 +283,9 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
 #pragma unroll
             for (int k = 2; k < RY + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
             cec_run<RY>(pv, cv, o);
-            const int kz = p - 3;
-            const bool store = kz >= sg.z0;
-            float *dst = I.out + (int64_t)wrapz(kz, I.nz) * I.plane + (int64_t)(y0 + yr) * I.nx + x0 + cx;
+            const bool store = p - 3 >= sg.z0;
+            const int kw = zw >= 3 ? zw - 3 : zw - 3 + I.nz;
+            float *dst = I.out + (int64_t)kw * I.plane + (int64_t)(y0 + yr) * I.nx + x0 + cx;
 #pragma unroll
             for (int i = 0; i < RY; ++i) {
                 const float c = czP[(yr + i) * TX + cx] * sz;
@@ -284,10 +295,13 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
             }
         };
 
-        issue(pfirst, 0);
+        int zw = wrapz(pfirst, I.nz);
+        issue(zw, 0);
         for (int p = pfirst; p <= plast; p += 2) {
-            plane(std::integral_constant<int, 0>(), p);
-            if (p + 1 <= plast) plane(std::integral_constant<int, 1>(), p + 1);
+            plane(std::integral_constant<int, 0>(), p, zw);
+            zw = zw + 1 == I.nz ? 0 : zw + 1;
+            if (p + 1 <= plast) plane(std::integral_constant<int, 1>(), p + 1, zw);
+            zw = zw + 1 == I.nz ? 0 : zw + 1;
         }
         __syncthreads();   // shared buffers are reused by the next segment
     }
@@ -296,7 +310,7 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
 
 // ============================================================ order z, y, x
 namespace zyx {
-constexpr int TX = 32, TY = 32, NT = 512, RX = 8, RY = 8;
+constexpr int TX = 32, TY = 32, NT = SL_ZYX_NT, RX = 8, RY = SL_ZYX_RY;
 constexpr int PH = TY + 6, PW = TX + 12;
 constexpr int SZ_PHI = PH * PW;                      // Phi and u_z (plane p-1): rows [-3, TY+3)
 constexpr int SZ_CY = (TY + 4) * PW;                 // u_y (plane p-3): rows [-2, TY+2)
@@ -308,7 +322,7 @@ constexpr size_t SMEM = sizeof(float) * (2 * SLOT + SZ_PHI + SZ_CX) + 128;
 }  // namespace zyx
 
 template <bool BATCH>
-__global__ void __launch_bounds__(zyx::NT, 1)
+__global__ void __launch_bounds__(zyx::NT, 512 / SL_ZYX_NT)
 k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict__ table, int ninst, int64_t total,
                unsigned *status)
 {
@@ -347,12 +361,12 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
         chCy.setup(tid, x0, y0, -2, -4, I.nx, I.ny);
         chCx.setup(tid, x0, y0, 0, -4, I.nx, I.ny);
 
-        auto issue = [&](int p, int slot) {
+        // pz: plane index of the bundle, already reduced modulo nz
+        auto issue = [&](int pz, int slot) {
             float *sb = buf + slot * SLOT;
             const int nz = I.nz;
-            const int pz = wrapz(p, nz);
             const int pz1 = pz == 0 ? nz - 1 : pz - 1;
-            const float *vk = I.vel + (int64_t)wrapz(p - 3, nz) * I.plane;
+            const float *vk = I.vel + (int64_t)(pz >= 3 ? pz - 3 : pz - 3 + nz) * I.plane;
             chPhi.issue(sb, I.in + (int64_t)pz * I.plane);
             chPhi.issue(sb + SZ_PHI, I.vel + 2 * I.ncell + (int64_t)pz1 * I.plane);
             chCy.issue(sb + 2 * SZ_PHI, vk + I.ncell);
@@ -364,12 +378,12 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
 #pragma unroll
         for (int j = 0; j < NCOL; ++j) win[j].init();
 
-        auto plane = [&](auto PC, int p) {
+        auto plane = [&](auto PC, int p, int zw) {
             constexpr int P = decltype(PC)::value;
             const int slot = (p - pfirst) & 1;
             cp_async_wait_all();
             __syncthreads();
-            if (p < plast) issue(p + 1, slot ^ 1);
+            if (p < plast) issue(zw + 1 == I.nz ? 0 : zw + 1, slot ^ 1);
             const float *sb = buf + slot * SLOT;
             const float *phiP = sb, *czP = sb + SZ_PHI, *cyP = sb + 2 * SZ_PHI, *cxP = sb + 2 * SZ_PHI + SZ_CY;
             // ---- z sweep on the halo-widened columns
@@ -384,8 +398,8 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
                 }
             }
             __syncthreads();
-            const int kz = p - 3;
-            if (kz < sg.z0) return;
+            if (p - 3 < sg.z0) return;
+            const int kw = zw >= 3 ? zw - 3 : zw - 3 + I.nz;
             // ---- y sweep: columns x in [-3, TX+3), rows [0, TY) -> sS2
             for (int r = tid; r < (TX + 6) * (TY / RY); r += NT) {
                 const int col = r % (TX + 6) + 1, yr = (r / (TX + 6)) * RY;
@@ -427,17 +441,20 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
 #pragma unroll
                 for (int k = 2; k < RX + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
                 cec_run<RX>(pv, cv, o);
-                float4 *dst = reinterpret_cast<float4 *>(I.out + (int64_t)wrapz(kz, I.nz) * I.plane +
-                                                         (int64_t)(y0 + row) * I.nx + x0 + xr);
+                float4 *dst = reinterpret_cast<float4 *>(I.out + (int64_t)kw * I.plane + (int64_t)(y0 + row) * I.nx +
+                                                         x0 + xr);
                 dst[0] = make_float4(o[0], o[1], o[2], o[3]);
                 dst[1] = make_float4(o[4], o[5], o[6], o[7]);
             }
         };
 
-        issue(pfirst, 0);
+        int zw = wrapz(pfirst, I.nz);
+        issue(zw, 0);
         for (int p = pfirst; p <= plast; p += 2) {
-            plane(std::integral_constant<int, 0>(), p);
-            if (p + 1 <= plast) plane(std::integral_constant<int, 1>(), p + 1);
+            plane(std::integral_constant<int, 0>(), p, zw);
+            zw = zw + 1 == I.nz ? 0 : zw + 1;
+            if (p + 1 <= plast) plane(std::integral_constant<int, 1>(), p + 1, zw);
+            zw = zw + 1 == I.nz ? 0 : zw + 1;
         }
         __syncthreads();
     }
