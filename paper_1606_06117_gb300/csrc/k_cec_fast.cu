@@ -173,14 +173,20 @@ struct Chunks {
 #define SL_XYZ_MINB 2      // CTAs per SM the x,y,z kernel is compiled for
 #endif
 #ifndef SL_ZYX_NT
-#define SL_ZYX_NT 512      // threads of the z,y,x kernel
+#define SL_ZYX_NT 256      // threads of the z,y,x kernel
+#endif
+#ifndef SL_ZYX_RX
+#define SL_ZYX_RX 8        // x-sweep run length of the z,y,x kernel
+#endif
+#ifndef SL_XYZ_RX
+#define SL_XYZ_RX 8        // x-sweep run length of the x,y,z kernel
 #endif
 #ifndef SL_ZYX_RY
 #define SL_ZYX_RY 8        // y-sweep run length of the z,y,x kernel
 #endif
 
 namespace xyz {
-constexpr int TX = 32, TY = 32, NT = 256, RX = 8, RY = 4;
+constexpr int TX = 32, TY = 32, NT = 256, RX = SL_XYZ_RX, RY = 4;
 constexpr int PH = TY + 6, PW = TX + 12;              // Phi / u_x rows [-3, TY+3), x [-4, TX+4), stride 44
 constexpr int SZ_PHI = PH * PW;
 constexpr int SZ_CY = (TY + 4) * TX;                  // u_y rows [-2, TY+2), x [0, TX)
@@ -271,8 +277,8 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
                 for (int k = 2; k < RX + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
                 cec_run<RX>(pv, cv, o);
                 float4 *dst = reinterpret_cast<float4 *>(sS1 + row * TX + xr);
-                dst[0] = make_float4(o[0], o[1], o[2], o[3]);
-                dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+#pragma unroll
+                for (int k = 0; k < RX / 4; ++k) dst[k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
             }
             __syncthreads();
             float pv[RY + 6], cv[RY + 4], o[RY];
@@ -310,7 +316,7 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
 
 // ============================================================ order z, y, x
 namespace zyx {
-constexpr int TX = 32, TY = 32, NT = SL_ZYX_NT, RX = 8, RY = SL_ZYX_RY;
+constexpr int TX = 32, TY = 32, NT = SL_ZYX_NT, RX = SL_ZYX_RX, RY = SL_ZYX_RY;
 constexpr int PH = TY + 6, PW = TX + 12;
 constexpr int SZ_PHI = PH * PW;                      // Phi and u_z (plane p-1): rows [-3, TY+3)
 constexpr int SZ_CY = (TY + 4) * PW;                 // u_y (plane p-3): rows [-2, TY+2)
@@ -443,8 +449,8 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
                 cec_run<RX>(pv, cv, o);
                 float4 *dst = reinterpret_cast<float4 *>(I.out + (int64_t)kw * I.plane + (int64_t)(y0 + row) * I.nx +
                                                          x0 + xr);
-                dst[0] = make_float4(o[0], o[1], o[2], o[3]);
-                dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+#pragma unroll
+                for (int k = 0; k < RX / 4; ++k) dst[k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
             }
         };
 
