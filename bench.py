@@ -299,6 +299,11 @@ def run_ours(args):
     extras = {}
     if not args.no_extras and rank == 0:
         extras = side_measurements(torch, sl, dev, stream, n, phi, vel, sp, dt)
+        del a, b
+        torch.cuda.empty_cache()
+        extras["batched_c3"] = batched_measurement(torch, sl, stream)
+        torch.cuda.empty_cache()
+        extras["deformation_c5"] = deformation_measurement(torch, sl, stream)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -367,6 +372,90 @@ def side_measurements(torch, sl, dev, stream, n, phi, vel, sp, dt):
                        "roundtrip_rel_l2_100_100": rel}
     out["schemes"] = rates
     return out
+
+
+def batched_measurement(torch, sl, stream, steps=20):
+    """48 independent grids of sizes drawn from {64..192}^3 (ABC or Taylor-Green
+    velocity, amplitudes in [0.5, 1.5], random-mode scalar, CFL 0.8): one
+    persistent launch per step (captured in a CUDA graph) against 48 separate
+    sl_advect launches per step."""
+    from paper_1606_06117_gb300 import workloads as W
+    insts = W.draw_batch(48, seed=0)
+    recs, keep, cells = [], [], 0
+    for inst in insts:
+        phi, vel = W.instance_fields(inst, device="cuda", dtype=torch.float32)
+        n = inst.n
+        sp = [2 * math.pi / n] * 3
+        umax = float(vel.abs().amax())
+        dt = 0.8 * sp[0] / umax
+        a, b = phi, torch.empty_like(phi)
+        keep.append((a, b, vel, n, sp, dt))
+        recs.append(sl.Instance(a.data_ptr(), b.data_ptr(), vel.data_ptr(), (n, n, n), tuple(sp), dt))
+        cells += n ** 3
+    h = sl.sl_batch_create(recs)
+    try:
+        sl.sl_batch_step(h, 0, stream)
+        sl.sl_batch_step(h, 1, stream)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            cap = torch.cuda.current_stream()
+            sl.sl_batch_step(h, 0, cap)
+            sl.sl_batch_step(h, 1, cap)
+        for _ in range(3):
+            g.replay()
+        ms_b = time_steps(torch, stream, lambda k: g.replay(), steps) / 2.0
+
+        def plain(k):
+            for a, b, vel, n, sp, dt in keep:
+                src, dst = (a, b) if k % 2 == 0 else (b, a)
+                sl.sl_advect(dst, src, vel, 3, [n, n, n], sp, dt, sl.CEC, sl.F32, k & 1, stream)
+        plain(0)
+        plain(1)
+        ms_p = time_steps(torch, stream, plain, 2 * steps)
+    finally:
+        sl.sl_batch_destroy(h)
+    return {"instances": len(insts), "cells_per_step": cells,
+            "batched_graph": {"gcell_s": cells / (ms_b * 1e-3) / 1e9, "ms_per_step": ms_b},
+            "plain_48_launches": {"gcell_s": cells / (ms_p * 1e-3) / 1e9, "ms_per_step": ms_p}}
+
+
+def deformation_measurement(torch, sl, stream, n=512, total_steps=2000, timed=20):
+    """Time-reversing deformation flow on [0,1)^3 at n^3: the three velocity
+    components of u(t=0) and a random-mode scalar advected with the CEC step,
+    u scaled by cos(pi t / T) over T = total_steps steps (CFL 0.8 at t = 0), so
+    that every field returns to its initial value at t = T.  Reports
+    field-cell-updates per second of sl_advect_multi and the relative L2 error
+    of each field at t = T."""
+    from paper_1606_06117_gb300 import workloads as W
+    shape = (n, n, n)
+    vel = W.deformation_velocity(shape, device="cuda", dtype=torch.float32)
+    scal = W.random_modes(shape, W.draw_modes(3, 32, 8, seed=5), length=1.0, device="cuda", dtype=torch.float32)
+    f0 = [vel[0].clone(), vel[1].clone(), vel[2].clone(), scal]
+    sp = [1.0 / n] * 3
+    umax = float(vel.abs().amax())
+    dt = 0.8 * sp[0] / umax
+    T = total_steps * dt
+    cur = [f.clone() for f in f0]
+    nxt = [torch.empty_like(f) for f in f0]
+
+    def step(k):
+        scale = math.cos(math.pi * (k + 0.5) * dt / T)
+        sl.sl_advect_multi(nxt, cur, vel, 3, [n, n, n], sp, dt * scale, sl.CEC, sl.F32, k & 1, stream)
+        cur[:], nxt[:] = nxt[:], cur[:]
+    for k in range(2):
+        step(k)
+    torch.cuda.synchronize()
+    ms = time_steps(torch, stream, lambda k: step(2 + k), timed)
+    # accuracy: the full forward-and-back run from the initial fields
+    cur[:] = [f.clone() for f in f0]
+    for k in range(total_steps):
+        step(k)
+    torch.cuda.synchronize()
+    errs = [sl.sl_norms(c, f, f.numel(), sl.F32, stream)[2] for c, f in zip(cur, f0)]
+    return {"grid": [n, n, n], "fields": 4, "steps_T": total_steps,
+            "field_gcell_s": 4 * n ** 3 / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+            "rel_l2_at_T": {"u": errs[0], "v": errs[1], "w": errs[2], "scalar": errs[3]}}
 
 
 def main():
