@@ -219,6 +219,69 @@ int sl_autotune(void *out, const void *in, const void *vel, int ndim,
                 const int64_t dims[3], const double spacing[3], double dt,
                 int dtype, int *tile_z, void *stream);
 
+/* --------------------------------------------------------------------------
+ * Learned one-pass corrector (no counterpart in the paper: a throughput form
+ * of the third-order step whose error is judged against the plain scheme).
+ *
+ * One learned step is Phi_new = L_U[Phi] + s * MLP(x), where L_U[Phi] is the
+ * multilinear (CIR) value at the departure point (Sec. 3, eq. CIR2D), and the
+ * MLP (67 -> 64 -> 64 -> 1, ReLU, BF16 operands with FP32 accumulation on the
+ * tensor cores) reads x = the cell's 4 x 4 x 4 upwind neighbourhood
+ * Phi(b - 1 .. b + 2) around the departure base b = min(floor(i - C), i),
+ * shifted by L_U[Phi] and divided by s = max |Phi_k - L_U[Phi]|, plus the three
+ * fractional offsets f - 1/2.  It is trained on pairs produced by the plain
+ * third-order step (eqs. intro:CEC, intro:CECcoef): target (CEC - L_U[Phi])/s.
+ *
+ * Parameter vector (FP32, sl_corrector_param_count() = 8577 values):
+ * W1 (64 x 67, row-major), b1 (64), W2 (64 x 64), b2 (64), w3 (64), b3 (1).
+ */
+typedef struct sl_corrector sl_corrector;
+
+int sl_corrector_param_count(void);
+/* He-initialised weights from a seeded generator; device buffers owned by c. */
+int sl_corrector_create(sl_corrector **out, uint64_t seed);
+int sl_corrector_destroy(sl_corrector *c);
+int sl_corrector_get_params(sl_corrector *c, float *host, int n);
+/* Also clears the fallback flag. */
+int sl_corrector_set_params(sl_corrector *c, const float *host, int n);
+/*
+ * Append nsamples training rows taken at pseudo-random cells (seeded) of the
+ * FP32 3D field phi with velocity vel: 67 inputs and the target
+ * (target - L_U[Phi]) / s, where target is the plain SL_CEC step of phi
+ * computed by the caller with the same vel, spacing and dt.  The corrector
+ * keeps the rows on the device (grown as needed).
+ */
+int sl_corrector_add_samples(sl_corrector *c, const void *phi, const void *target, const void *vel,
+                             const int64_t dims[3], const double spacing[3], double dt,
+                             int nsamples, uint64_t seed, void *stream);
+/* Copy rows [first, first + n) of the training set to host (68 floats each). */
+int sl_corrector_get_rows(sl_corrector *c, float *host, int64_t first, int64_t n);
+/*
+ * iters Adam steps (beta 0.9 / 0.999) on minibatches of batch rows drawn with
+ * the seed; FP32 forward and backward on the CUDA cores.  *last_loss (may be
+ * NULL) receives the mean squared error of the last minibatch.  Synchronous.
+ */
+int sl_corrector_train(sl_corrector *c, int iters, int batch, float lr, uint64_t seed,
+                       float *last_loss, void *stream);
+/* Clear the fallback flag (learned steps resume). */
+int sl_corrector_reset(sl_corrector *c);
+/*
+ * One step with the corrector: FP32 fields, ndim = 3, dims[0] % 32 == 0,
+ * dims[1] % 4 == 0, dims[2] >= 3.  With check == 0 the learned step runs
+ * (or the plain SL_CEC step with step_parity once the corrector has fallen
+ * back).  With check != 0 the plain SL_CEC and SL_BEC steps of the same input
+ * are also computed; the learned error is ||learned - CEC|| / ||CEC|| and the
+ * plain error ||BEC - CEC|| / ||CEC|| (the distance of the second-order
+ * scheme from the third-order one).  If the learned error exceeds
+ * fallback_ratio times the plain error, out receives the plain step and the
+ * corrector falls back for good (until sl_corrector_reset).  errs (may be NULL)
+ * receives the two errors; *used_plain (may be NULL) the fallback flag.
+ * A checked step synchronises the stream.
+ */
+int sl_advect_learned(sl_corrector *c, void *out, const void *in, const void *vel, int ndim,
+                      const int64_t dims[3], const double spacing[3], double dt, int step_parity,
+                      int check, double fallback_ratio, int *used_plain, double errs[2], void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,10 @@ STATUS = {0: "SL_OK", -1: "SL_ERR_ARG", -2: "SL_ERR_ALIAS", -3: "SL_ERR_CFL", -4
 #: every symbol include/sl.h declares
 EXPORTS = ("sl_version", "sl_last_error", "sl_init", "sl_advect", "sl_advect_multi", "sl_advect_host",
            "sl_release_host_staging", "sl_courant_max", "sl_norms", "sl_device_status", "sl_batch_create",
-           "sl_batch_step", "sl_batch_destroy", "sl_autotune", "sl_norms_static")
+           "sl_batch_step", "sl_batch_destroy", "sl_autotune", "sl_norms_static",
+           "sl_corrector_param_count", "sl_corrector_create", "sl_corrector_destroy", "sl_corrector_get_params",
+           "sl_corrector_set_params", "sl_corrector_add_samples", "sl_corrector_get_rows", "sl_corrector_train",
+           "sl_corrector_reset", "sl_advect_learned")
 
 
 class SLError(RuntimeError):
@@ -80,6 +83,16 @@ def load(path: str | None = None):
             "sl_batch_step": ([vp, i, vp], i),
             "sl_batch_destroy": ([vp], i),
             "sl_autotune": ([vp, vp, vp, i, i64p, dp, d, i, ctypes.POINTER(i), vp], i),
+            "sl_corrector_param_count": ([], i),
+            "sl_corrector_create": ([ctypes.POINTER(vp), ctypes.c_uint64], i),
+            "sl_corrector_destroy": ([vp], i),
+            "sl_corrector_get_params": ([vp, ctypes.POINTER(ctypes.c_float), i], i),
+            "sl_corrector_set_params": ([vp, ctypes.POINTER(ctypes.c_float), i], i),
+            "sl_corrector_add_samples": ([vp, vp, vp, vp, i64p, dp, d, i, ctypes.c_uint64, vp], i),
+            "sl_corrector_get_rows": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int64, ctypes.c_int64], i),
+            "sl_corrector_train": ([vp, i, i, ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(ctypes.c_float), vp], i),
+            "sl_corrector_reset": ([vp], i),
+            "sl_advect_learned": ([vp, vp, vp, vp, i, i64p, dp, d, i, i, d, ctypes.POINTER(i), dp, vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -206,6 +219,67 @@ def sl_autotune(out, inp, vel, ndim, dims, spacing, dt, dtype, stream=None):
     _check(load().sl_autotune(_ptr(out), _ptr(inp), _ptr(vel), ndim, _i64(dims), _f64(spacing), float(dt),
                               int(dtype), ctypes.byref(tz), _stream(stream)))
     return tz.value
+
+
+def sl_corrector_param_count():
+    return load().sl_corrector_param_count()
+
+
+def sl_corrector_create(seed=0):
+    h = ctypes.c_void_p()
+    _check(load().sl_corrector_create(ctypes.byref(h), int(seed)))
+    return h
+
+
+def sl_corrector_destroy(c):
+    return _check(load().sl_corrector_destroy(c))
+
+
+def sl_corrector_get_params(c):
+    import numpy as np
+    out = np.empty(sl_corrector_param_count(), dtype=np.float32)
+    _check(load().sl_corrector_get_params(c, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size))
+    return out
+
+
+def sl_corrector_set_params(c, params):
+    import numpy as np
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    return _check(load().sl_corrector_set_params(c, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
+
+
+def sl_corrector_add_samples(c, phi, target, vel, dims, spacing, dt, nsamples, seed=0, stream=None):
+    return _check(load().sl_corrector_add_samples(c, _ptr(phi), _ptr(target), _ptr(vel), _i64(dims), _f64(spacing),
+                                                  float(dt), int(nsamples), int(seed), _stream(stream)))
+
+
+def sl_corrector_get_rows(c, first, n):
+    import numpy as np
+    out = np.empty((n, 68), dtype=np.float32)
+    _check(load().sl_corrector_get_rows(c, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), int(first), int(n)))
+    return out
+
+
+def sl_corrector_train(c, iters, batch, lr, seed=0, stream=None):
+    loss = ctypes.c_float()
+    _check(load().sl_corrector_train(c, int(iters), int(batch), float(lr), int(seed), ctypes.byref(loss),
+                                     _stream(stream)))
+    return loss.value
+
+
+def sl_corrector_reset(c):
+    return _check(load().sl_corrector_reset(c))
+
+
+def sl_advect_learned(c, out, inp, vel, ndim, dims, spacing, dt, step_parity=0, check=0, fallback_ratio=2.0,
+                      stream=None):
+    """Returns (used_plain, (learned_error, plain_error) or None)."""
+    used = ctypes.c_int()
+    errs = (ctypes.c_double * 2)(-1.0, -1.0)
+    _check(load().sl_advect_learned(c, _ptr(out), _ptr(inp), _ptr(vel), ndim, _i64(dims), _f64(spacing), float(dt),
+                                    int(step_parity), int(check), float(fallback_ratio), ctypes.byref(used), errs,
+                                    _stream(stream)))
+    return used.value, ((errs[0], errs[1]) if check else None)
 
 
 # ------------------------------------------------------------- conveniences
