@@ -304,6 +304,8 @@ def run_ours(args):
         extras["batched_c3"] = batched_measurement(torch, sl, stream)
         torch.cuda.empty_cache()
         extras["deformation_c5"] = deformation_measurement(torch, sl, stream)
+        torch.cuda.empty_cache()
+        extras["learned_c4"] = learned_measurement(torch, sl, stream)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -418,6 +420,75 @@ def batched_measurement(torch, sl, stream, steps=20):
     return {"instances": len(insts), "cells_per_step": cells,
             "batched_graph": {"gcell_s": cells / (ms_b * 1e-3) / 1e9, "ms_per_step": ms_b},
             "plain_48_launches": {"gcell_s": cells / (ms_p * 1e-3) / 1e9, "ms_per_step": ms_p}}
+
+
+def learned_measurement(torch, sl, stream, n=256, steps=500, check_every=25):
+    """Learned corrector (67-64-64-1 BF16 MLP on the tensor cores): trained on
+    128^3 ABC / Taylor-Green random-mode fields advected by the plain CEC step,
+    then run on the n^3 ABC workload for `steps` steps with a plain-scheme check
+    every `check_every` steps and fallback above 2x the plain error.  Reports
+    the learned and plain step rates, the training loss, the checked errors and
+    the 100-forward / 100-reverse round-trip error of each path."""
+    from paper_1606_06117_gb300 import workloads as W
+    c = sl.sl_corrector_create(0)
+    try:
+        m = 128
+        spm = [2 * math.pi / m] * 3
+        flows = [W.abc_velocity((m,) * 3, device="cuda", dtype=torch.float32),
+                 W.abc_velocity((m,) * 3, 1.3, 0.7, 1.1, device="cuda", dtype=torch.float32),
+                 W.taylor_green_velocity((m,) * 3, 1.0, device="cuda", dtype=torch.float32),
+                 W.taylor_green_velocity((m,) * 3, 1.4, device="cuda", dtype=torch.float32)]
+        t0 = time.perf_counter()
+        for i, v in enumerate(flows):
+            dtm = 0.8 * spm[0] / float(v.abs().amax())
+            cur = W.random_modes((m,) * 3, W.draw_modes(3, 32, 8, seed=20 + i), device="cuda", dtype=torch.float32)
+            for k in range(6):
+                nxt = sl.advect(cur, v, dtm, spm, "CEC", 0)
+                sl.sl_corrector_add_samples(c, cur, nxt, v, [m] * 3, spm, dtm, 100000, seed=1000 * i + k)
+                cur = sl.advect(cur, v, dtm, spm, "CEC", k)
+        loss0 = sl.sl_corrector_train(c, 1, 4096, 1e-3, seed=1)
+        loss = sl.sl_corrector_train(c, 3000, 4096, 1e-3, seed=2)
+        train_s = time.perf_counter() - t0
+        # evaluation on the bench workload
+        phi, vel, sp, dt = workload(n, "cuda", torch)
+        dims = [n] * 3
+        a, b = phi.clone(), torch.empty_like(phi)
+
+        def lstep(k):
+            sl.sl_advect_learned(c, b, a, vel, 3, dims, sp, dt, k & 1, 0, 2.0, stream)
+        lstep(0)
+        lstep(1)
+        ms_l = time_steps(torch, stream, lstep, 50)
+        checks, fell_at = [], None
+        x, y = phi.clone(), torch.empty_like(phi)
+        for k in range(steps):
+            chk = (k % check_every) == 0
+            used, errs = sl.sl_advect_learned(c, y, x, vel, 3, dims, sp, dt, k & 1, int(chk), 2.0, stream)
+            if chk:
+                checks.append({"step": k, "learned_err": errs[0], "plain_err": errs[1], "plain_used": used})
+            if used and fell_at is None:
+                fell_at = k
+            x, y = y, x
+        # round-trip accuracy of each path (learned path without checks)
+        sl.sl_corrector_reset(c)
+        rt = {}
+        for name in ("learned", "plain"):
+            x, y = phi.clone(), torch.empty_like(phi)
+            for k in range(200):
+                d = dt if k < 100 else -dt
+                if name == "learned":
+                    sl.sl_advect_learned(c, y, x, vel, 3, dims, sp, d, k & 1, 0, 2.0, stream)
+                else:
+                    sl.sl_advect(y, x, vel, 3, dims, sp, d, sl.CEC, sl.F32, k & 1, stream)
+                x, y = y, x
+            rt[name] = sl.sl_norms(x, phi, phi.numel(), sl.F32, stream)[2]
+    finally:
+        sl.sl_corrector_destroy(c)
+    return {"train": {"grid": [128] * 3, "rows": 4 * 6 * 100000, "iters": 3000, "batch": 4096,
+                      "loss_first": loss0, "loss_last": loss, "seconds": train_s},
+            "learned_gcell_s": n ** 3 / (ms_l * 1e-3) / 1e9, "learned_ms_per_step": ms_l,
+            "steps": steps, "check_every": check_every, "fell_back_at_step": fell_at, "checks": checks[:6],
+            "roundtrip_rel_l2_100_100": rt}
 
 
 def deformation_measurement(torch, sl, stream, n=512, total_steps=2000, timed=20):
