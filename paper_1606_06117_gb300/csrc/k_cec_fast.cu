@@ -51,6 +51,50 @@ __device__ __forceinline__ void cec_run(const float (&p)[R + 6], const float (&c
     }
 }
 
+// The same run when every Courant number of it has the sign S (+1 or -1):
+// the upwind side is fixed, so no comparison or selection is needed.
+template <int R, int S>
+__device__ __forceinline__ void cec_run_signed(const float (&p)[R + 6], const float (&c)[R + 4], float (&o)[R])
+{
+    float dp[R + 5];
+#pragma unroll
+    for (int j = 0; j < R + 5; ++j) dp[j] = p[j + 1] - p[j];
+    float l[R + 4];
+#pragma unroll
+    for (int m = 0; m < R + 4; ++m) l[m] = -c[m] * (S > 0 ? dp[m] : dp[m + 1]);
+    float e[R + 3];
+#pragma unroll
+    for (int k = 0; k < R + 3; ++k) e[k] = dp[k + 1] + (l[k + 1] - l[k]);
+    float del[R + 2];
+#pragma unroll
+    for (int q = 0; q < R + 2; ++q) del[q] = -l[q + 1] - c[q + 1] * (S > 0 ? e[q + 1] : e[q]);
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const float U = S > 0 ? c[i + 2] : -c[i + 2], d0 = del[i + 1];
+        const float dup = S > 0 ? del[i] : del[i + 2];
+        o[i] = (p[i + 3] + l[i + 2]) + (2.f * d0 + dup + U * (dup - d0)) * (1.f / 6.f);
+    }
+}
+
+// Picks the sign-specialised form when the whole warp's runs share one sign.
+template <int R>
+__device__ __forceinline__ void cec_run_auto(const float (&p)[R + 6], const float (&c)[R + 4], float (&o)[R])
+{
+    bool pos = true, neg = true;
+#pragma unroll
+    for (int k = 0; k < R + 4; ++k) {
+        pos &= c[k] > 0.f;
+        neg &= c[k] < 0.f;
+    }
+    const unsigned am = __activemask();
+    if (__all_sync(am, pos))
+        cec_run_signed<R, 1>(p, c, o);
+    else if (__all_sync(am, neg))
+        cec_run_signed<R, -1>(p, c, o);
+    else
+        cec_run<R>(p, c, o);
+}
+
 // z sweep window of one column.  push<P>(phi_p, c_{p-1}) returns the result at
 // plane p-3; P alternates 0, 1 so that two-deep values change roles instead of
 // being moved.
@@ -90,7 +134,58 @@ struct ZCol {
         dl[P] = dn2;
         return out;
     }
+
+    // push<P> when the Courant numbers at p-3, p-2 and p-1 all have sign S
+    template <int P, int S>
+    __device__ __forceinline__ float push_signed(float phi, float cn)
+    {
+        const float dn = phi - ph;
+        const float ln = -cn * (S > 0 ? d : dn);
+        const float Ln = ph + ln;
+        const float en = d + (ln - l);
+        const float c2 = c[P ^ 1];
+        const float dn2 = -l - c2 * (S > 0 ? en : e);
+        const float U = S > 0 ? c[P] : -c[P], d0 = dl[P ^ 1];
+        const float dup = S > 0 ? dl[P] : dn2;
+        const float out = L[P] + (2.f * d0 + dup + U * (dup - d0)) * (1.f / 6.f);
+        ph = phi;
+        d = dn;
+        l = ln;
+        e = en;
+        c[P] = cn;
+        L[P] = Ln;
+        dl[P] = dn2;
+        return out;
+    }
+
+    template <int P>
+    __device__ __forceinline__ bool sign_pos(float cn) const { return cn > 0.f && c[0] > 0.f && c[1] > 0.f; }
+    template <int P>
+    __device__ __forceinline__ bool sign_neg(float cn) const { return cn < 0.f && c[0] < 0.f && c[1] < 0.f; }
 };
+
+// Pushes one plane into N windows, sign-specialised when the whole warp agrees.
+template <int P, int N>
+__device__ __forceinline__ void push_all(ZCol (&win)[N], const float (&phi)[N], const float (&cn)[N], float (&out)[N])
+{
+    bool pos = true, neg = true;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        pos &= win[i].template sign_pos<P>(cn[i]);
+        neg &= win[i].template sign_neg<P>(cn[i]);
+    }
+    const unsigned am = __activemask();
+    if (__all_sync(am, pos)) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) out[i] = win[i].template push_signed<P, 1>(phi[i], cn[i]);
+    } else if (__all_sync(am, neg)) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) out[i] = win[i].template push_signed<P, -1>(phi[i], cn[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) out[i] = win[i].template push<P>(phi[i], cn[i]);
+    }
+}
 
 // ---------------------------------------------------------------- geometry
 struct Seg {
@@ -275,7 +370,7 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
                 for (int k = 0; k < RX + 4; ++k) cv[k] = blk[k + 2] * sx;
 #pragma unroll
                 for (int k = 2; k < RX + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
-                cec_run<RX>(pv, cv, o);
+                cec_run_auto<RX>(pv, cv, o);
                 float4 *dst = reinterpret_cast<float4 *>(sS1 + row * TX + xr);
 #pragma unroll
                 for (int k = 0; k < RX / 4; ++k) dst[k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
@@ -288,16 +383,20 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
             for (int k = 0; k < RY + 4; ++k) cv[k] = cyP[(yr + k) * TX + cx] * sy;
 #pragma unroll
             for (int k = 2; k < RY + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
-            cec_run<RY>(pv, cv, o);
+            cec_run_auto<RY>(pv, cv, o);
             const bool store = p - 3 >= sg.z0;
             const int kw = zw >= 3 ? zw - 3 : zw - 3 + I.nz;
             float *dst = I.out + (int64_t)kw * I.plane + (int64_t)(y0 + yr) * I.nx + x0 + cx;
+            float cz[RY], res[RY];
 #pragma unroll
             for (int i = 0; i < RY; ++i) {
-                const float c = czP[(yr + i) * TX + cx] * sz;
-                bad |= fabsf(c) > 1.f;
-                const float v = win[i].push<P>(o[i], c);
-                if (store) dst[(int64_t)i * I.nx] = v;
+                cz[i] = czP[(yr + i) * TX + cx] * sz;
+                bad |= fabsf(cz[i]) > 1.f;
+            }
+            push_all<P, RY>(win, o, cz, res);
+            if (store) {
+#pragma unroll
+                for (int i = 0; i < RY; ++i) dst[(int64_t)i * I.nx] = res[i];
             }
         };
 
@@ -409,7 +508,7 @@ k_cec_xyz_wide(const __grid_constant__ FastInst one, const FastInst *__restrict_
                 for (int k = 0; k < RX + 4; ++k) cv[k] = blk[k + 2] * sx;
 #pragma unroll
                 for (int k = 2; k < RX + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
-                cec_run<RX>(pv, cv, o);
+                cec_run_auto<RX>(pv, cv, o);
                 *reinterpret_cast<float4 *>(sS1 + row * TX + xr) = make_float4(o[0], o[1], o[2], o[3]);
             }
             __syncthreads();
@@ -421,7 +520,7 @@ k_cec_xyz_wide(const __grid_constant__ FastInst one, const FastInst *__restrict_
                 for (int k = 0; k < RY + 4; ++k) cv[k] = cyP[(yyr + k) * TX + ycx] * sy;
 #pragma unroll
                 for (int k = 2; k < RY + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
-                cec_run<RY>(pv, cv, o);
+                cec_run_auto<RY>(pv, cv, o);
 #pragma unroll
                 for (int i = 0; i < RY; ++i) sS2[(yyr + i) * TX + ycx] = o[i];
             }
@@ -555,7 +654,7 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
 #pragma unroll
                     for (int k = 2; k < RY + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
                 }
-                cec_run<RY>(pv, cv, o);
+                cec_run_auto<RY>(pv, cv, o);
 #pragma unroll
                 for (int i = 0; i < RY; ++i) sS2[(yr + i) * PW + col] = o[i];
             }
@@ -583,7 +682,7 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
                 for (int k = 0; k < RX + 4; ++k) cv[k] = blk[k + 2] * sx;
 #pragma unroll
                 for (int k = 2; k < RX + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
-                cec_run<RX>(pv, cv, o);
+                cec_run_auto<RX>(pv, cv, o);
                 float4 *dst = reinterpret_cast<float4 *>(I.out + (int64_t)kw * I.plane + (int64_t)(y0 + row) * I.nx +
                                                          x0 + xr);
 #pragma unroll
