@@ -560,7 +560,6 @@ constexpr int SZ_CX = TY * PW;                       // u_x (plane p-3): rows [0
 constexpr int SLOT = 2 * SZ_PHI + SZ_CY + SZ_CX;
 constexpr int NZC = (TX + 6) * (TY + 6);             // z-swept columns (x, y in [-3, T+3))
 constexpr int NCOL = (NZC + NT - 1) / NT;
-static_assert(NT <= NZC, "every thread owns at least one z column");
 constexpr size_t SMEM = sizeof(float) * (2 * SLOT + SZ_PHI + SZ_CX) + 128;
 }  // namespace zyx
 
@@ -589,13 +588,10 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
 
     // per-thread z columns: staged offsets (row = y + 3, col = x + 4)
     int zoff[NCOL];
-    unsigned zvalid = 0;
 #pragma unroll
     for (int j = 0; j < NCOL; ++j) {
         const int r = tid + j * NT;
-        const int rr = r < NZC ? r : tid;   // tid < NZC always holds
-        zoff[j] = (rr / (TX + 6)) * PW + (rr % (TX + 6)) + 1;
-        if (r < NZC) zvalid |= 1u << j;
+        zoff[j] = r < NZC ? (r / (TX + 6)) * PW + (r % (TX + 6)) + 1 : -1;
     }
 
     while (next_seg(tab, ninst, w, wend, hint, (double)total / (double)G, sg)) {
@@ -632,25 +628,15 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
             if (p < plast) issue(zw + 1 == I.nz ? 0 : zw + 1, slot ^ 1);
             const float *sb = buf + slot * SLOT;
             const float *phiP = sb, *czP = sb + SZ_PHI, *cyP = sb + 2 * SZ_PHI, *cxP = sb + 2 * SZ_PHI + SZ_CY;
-            // ---- z sweep on the halo-widened columns (slots past the end repeat
-            //      this thread's first column; their results are not stored)
-            {
-                float ph[NCOL], cz[NCOL], res[NCOL];
+            // ---- z sweep on the halo-widened columns
 #pragma unroll
-                for (int j = 0; j < NCOL; ++j) {
+            for (int j = 0; j < NCOL; ++j) {
+                if (zoff[j] >= 0) {
                     const int o = zoff[j];
-                    ph[j] = phiP[o];
-                    cz[j] = czP[o] * sz;
-                }
-                push_all<P, NCOL>(win, ph, cz, res);
-#pragma unroll
-                for (int j = 0; j < NCOL; ++j) {
-                    if (zvalid & (1u << j)) {
-                        const int o = zoff[j];
-                        sZ[o] = res[j];
-                        const int row = o / PW, col = o - row * PW;
-                        if (row >= 3 && row < TY + 3 && col >= 4 && col < TX + 4) bad |= fabsf(cz[j]) > 1.f;
-                    }
+                    const float c = czP[o] * sz;
+                    sZ[o] = win[j].push<P>(phiP[o], c);
+                    const int row = o / PW, col = o - row * PW;
+                    if (row >= 3 && row < TY + 3 && col >= 4 && col < TX + 4) bad |= fabsf(c) > 1.f;
                 }
             }
             __syncthreads();
