@@ -169,10 +169,12 @@ def test_norms_and_courant_reductions():
     assert cmax == pytest.approx(np.abs(courant(vel, sp, dt)).max(), rel=1e-15)
 
 
-@pytest.mark.parametrize("shape,parity", [((256, 256, 256), 0), ((256, 256, 256), 1)])
+@pytest.mark.parametrize("shape,parity", [((256, 256, 256), 0), ((256, 256, 256), 1),
+                                          ((512, 512, 512), 0), ((512, 512, 512), 1)])
 def test_full_size_sampled_parity(shape, parity):
     """The benchmark workload (256^3 ABC flow, 32-mode field, CFL 0.8) at full size in
-    the launch configuration the benchmark times, checked on 1500 sampled cells."""
+    the launch configuration the benchmark times, and the same flow at 512^3 (the
+    size of the four-field run), checked on 1500 sampled cells."""
     sp = [2 * math.pi / n for n in shape[::-1]]
     dt = 0.8 * sp[0] / 2.0
     phi = W.random_modes(shape, W.draw_modes(3, 32, 8, seed=0), device=DEV, dtype=torch.float32)
@@ -250,3 +252,23 @@ def test_fast_path_partitions_agree(parity):
         if parity == 0:
             ref = oracle_step(phi, vel, sp, dt, "CEC", 0)
             assert rel_l2(single.cpu().double().numpy(), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("parity", [0, 1])
+def test_deformation_512_sampled_parity(parity):
+    """The 512^3 time-reversing deformation flow of the four-field run, one multi-field
+    step at t = 0 (velocity components advected as fields), on sampled cells."""
+    n = 512
+    shape = (n, n, n)
+    vel = W.deformation_velocity(shape, device=DEV, dtype=torch.float32)
+    sp = [1.0 / n] * 3
+    dt = 0.8 * sp[0] / float(vel.abs().amax())
+    ins = [vel[0].clone(), vel[2].clone()]
+    outs = [torch.empty_like(f) for f in ins]
+    sl.sl_advect_multi(outs, ins, vel, 3, [n, n, n], sp, dt, sl.CEC, sl.F32, parity)
+    torch.cuda.synchronize()
+    cells = sample_cells(shape, 600, seed=21 + parity)
+    for f, o in zip(ins, outs):
+        ref = oracle_at_cells(f, vel, sp, dt, "CEC", parity, cells)
+        got = o[cells[:, 2], cells[:, 1], cells[:, 0]].cpu().double().numpy()
+        assert rel_l2(got, ref) <= 1e-5
