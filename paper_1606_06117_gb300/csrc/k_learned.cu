@@ -329,12 +329,13 @@ constexpr int HX = BX + 4, HY = BY + 4, HZ = 5;   // staged block, halo 2
 constexpr int A1_BYTES = MT * KP1 * 2, A2_BYTES = MT * NH * 2;
 constexpr int W1_BYTES = NH * KP1 * 2, W2_BYTES = NH * NH * 2;
 constexpr int BLK_FLOATS = HX * HY * HZ;
-// layout of the dynamic shared memory (bytes); operand regions padded so that
-// any reading of the core-matrix strides stays inside the allocation
-constexpr int S_A1 = 0, S_A2 = S_A1 + 2 * A1_BYTES, S_W1 = S_A2 + 2 * A2_BYTES, S_W2 = S_W1 + W1_BYTES;
+// layout of the dynamic shared memory (bytes); about 60 KB, so three CTAs fit
+// on an SM and take 384 of its 512 tensor-memory columns
+constexpr int S_A1 = 0, S_A2 = S_A1 + A1_BYTES, S_W1 = S_A2 + A2_BYTES, S_W2 = S_W1 + W1_BYTES;
 constexpr int S_F = S_W2 + W2_BYTES;                          // FP32: b1, b2, w3, b3
-constexpr int S_BLK = S_F + 4 * (3 * NH + 4);
-constexpr int S_BAR = S_BLK + 4 * BLK_FLOATS;
+constexpr int STAGE_FLOATS = BLK_FLOATS + 3 * MT;              // Phi block + the tile's three u components
+constexpr int S_BLK = S_F + 4 * (3 * NH + 4);                  // two stages (double buffer)
+constexpr int S_BAR = S_BLK + 2 * 4 * STAGE_FLOATS;
 constexpr int S_TM = S_BAR + 16;
 constexpr int SMEM_BYTES = S_TM + 16;
 
@@ -381,31 +382,49 @@ __global__ void __launch_bounds__(MT) k_learned_step(const float *__restrict__ p
 
     const int tiles_x = nx / BX, tiles_y = ny / BY;
     const int64_t ntiles = (int64_t)tiles_x * tiles_y * nz;
-    for (int64_t t = blockIdx.x; t < ntiles && !timeout; t += gridDim.x) {
+    // the Phi block x in [x0-2, x0+34), y in [y0-2, y0+6), z in [z-2, z+3) and
+    // the tile's velocity, staged with 4-byte cp.async one tile ahead
+    auto issue_block = [&](int64_t tt, int b) {
+        const int tx_ = (int)(tt % tiles_x);
+        const int ty_ = (int)((tt / tiles_x) % tiles_y);
+        const int z_ = (int)(tt / ((int64_t)tiles_x * tiles_y));
+        float *dst = blk + b * STAGE_FLOATS;
+        for (int i = tid; i < BLK_FLOATS; i += MT) {
+            const int bx = i % HX, by = (i / HX) % HY, bz = i / (HX * HY);
+            int gx = tx_ * BX - 2 + bx, gy = ty_ * BY - 2 + by, gz = z_ - 2 + bz;   // at most one period away
+            gx += gx < 0 ? nx : (gx >= nx ? -nx : 0);
+            gy += gy < 0 ? ny : (gy >= ny ? -ny : 0);
+            gz += gz < 0 ? nz : (gz >= nz ? -nz : 0);
+            cp_async4(dst + i, phi + (int64_t)gz * plane + (int64_t)gy * nx + gx);
+        }
+        const int64_t cell_ = (int64_t)z_ * plane + (int64_t)(ty_ * BY + tid / BX) * nx + tx_ * BX + tid % BX;
+        cp_async4(dst + BLK_FLOATS + tid, vel + cell_);
+        cp_async4(dst + BLK_FLOATS + MT + tid, vel + ncell + cell_);
+        cp_async4(dst + BLK_FLOATS + 2 * MT + tid, vel + 2 * ncell + cell_);
+        cp_async_commit();
+    };
+    if ((int64_t)blockIdx.x < ntiles) issue_block(blockIdx.x, 0);
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < ntiles && !timeout; t += gridDim.x, ++it) {
         const int tx = (int)(t % tiles_x);
         const int ty = (int)((t / tiles_x) % tiles_y);
         const int z = (int)(t / ((int64_t)tiles_x * tiles_y));
         const int x0 = tx * BX, y0 = ty * BY;
-        // ---- stage the block x in [x0-2, x0+34), y in [y0-2, y0+6), z in [z-2, z+3)
-        for (int i = tid; i < BLK_FLOATS; i += MT) {
-            const int bx = i % HX, by = (i / HX) % HY, bz = i / (HX * HY);
-            int gx = x0 - 2 + bx, gy = y0 - 2 + by, gz = z - 2 + bz;   // at most one period away
-            gx += gx < 0 ? nx : (gx >= nx ? -nx : 0);
-            gy += gy < 0 ? ny : (gy >= ny ? -ny : 0);
-            gz += gz < 0 ? nz : (gz >= nz ? -nz : 0);
-            blk[i] = phi[(int64_t)gz * plane + (int64_t)gy * nx + gx];
-        }
+        const float *sb = blk + (it & 1) * STAGE_FLOATS;
+        cp_async_wait_all();
         __syncthreads();
+        if (t + gridDim.x < ntiles) issue_block(t + gridDim.x, (it & 1) ^ 1);
         // ---- features of this thread's cell -> row tid of A1 (BF16)
         const int cxl = tid % BX, cyl = tid / BX;
         const int64_t cell = (int64_t)z * plane + (int64_t)(y0 + cyl) * nx + x0 + cxl;
-        const float cx = vel[cell] * sx, cy = vel[ncell + cell] * sy, cz = vel[2 * ncell + cell] * sz;
+        const float cx = sb[BLK_FLOATS + tid] * sx, cy = sb[BLK_FLOATS + MT + tid] * sy,
+                    cz = sb[BLK_FLOATS + 2 * MT + tid] * sz;
         if (fabsf(cx) > 1.f || fabsf(cy) > 1.f || fabsf(cz) > 1.f) atomicOr(status, 1u);
         const float ccx = fminf(fmaxf(cx, -1.f), 1.f), ccy = fminf(fmaxf(cy, -1.f), 1.f),
                     ccz = fminf(fmaxf(cz, -1.f), 1.f);
         auto at = [&](int xx, int yy, int zz) {
             // xx, yy, zz are global indices within 2 cells of the cell
-            return blk[((zz - z + 2) * HY + (yy - y0 + 2)) * HX + (xx - x0 + 2)];
+            return sb[((zz - z + 2) * HY + (yy - y0 + 2)) * HX + (xx - x0 + 2)];
         };
         float feat[NIN], m, s;
         cell_features(at, x0 + cxl, y0 + cyl, z, ccx, ccy, ccz, feat, m, s);
@@ -488,6 +507,7 @@ __global__ void __launch_bounds__(MT) k_learned_step(const float *__restrict__ p
         tc_fence_after();
         timeout = __syncthreads_or(timeout);
     }
+    cp_async_wait_all();   // a block prefetched for a tile that was not run
     if (timeout && tid == 0) atomicOr(status, 2u);
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem));
@@ -725,7 +745,7 @@ int sl_advect_learned(sl_corrector *c, void *out, const void *in, const void *ve
             smem_set[ctx->device] = 1;
         }
         const int64_t tiles = (dims[0] / BX) * (dims[1] / BY) * dims[2];
-        int grid = ctx->num_sms * 2;
+        int grid = ctx->num_sms * 3;
         if (grid > tiles) grid = (int)tiles;
         k_learned_step<<<grid, MT, SMEM_BYTES, st>>>(
             static_cast<const float *>(in), static_cast<float *>(dst), static_cast<const float *>(vel), (int)dims[0],
