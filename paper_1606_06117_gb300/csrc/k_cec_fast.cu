@@ -77,25 +77,22 @@ __device__ __forceinline__ void cec_run_signed(const float (&p)[R + 6], const fl
 }
 
 // Picks the sign-specialised form when the whole warp's runs share one sign.
-// Returns whether some Courant number of the run exceeds 1 in magnitude (the
-// run's minimum and maximum serve both tests).
 template <int R>
-__device__ __forceinline__ bool cec_run_auto(const float (&p)[R + 6], const float (&c)[R + 4], float (&o)[R])
+__device__ __forceinline__ void cec_run_auto(const float (&p)[R + 6], const float (&c)[R + 4], float (&o)[R])
 {
-    float lo = c[0], hi = c[0];
+    bool pos = true, neg = true;
 #pragma unroll
-    for (int k = 1; k < R + 4; ++k) {
-        lo = fminf(lo, c[k]);
-        hi = fmaxf(hi, c[k]);
+    for (int k = 0; k < R + 4; ++k) {
+        pos &= c[k] > 0.f;
+        neg &= c[k] < 0.f;
     }
     const unsigned am = __activemask();
-    if (__all_sync(am, lo > 0.f))
+    if (__all_sync(am, pos))
         cec_run_signed<R, 1>(p, c, o);
-    else if (__all_sync(am, hi < 0.f))
+    else if (__all_sync(am, neg))
         cec_run_signed<R, -1>(p, c, o);
     else
         cec_run<R>(p, c, o);
-    return fmaxf(-lo, hi) > 1.f;
 }
 
 // z sweep window of one column.  push<P>(phi_p, c_{p-1}) returns the result at
@@ -371,7 +368,9 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
                 }
 #pragma unroll
                 for (int k = 0; k < RX + 4; ++k) cv[k] = blk[k + 2] * sx;
-                bad |= cec_run_auto<RX>(pv, cv, o);
+#pragma unroll
+                for (int k = 2; k < RX + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
+                cec_run_auto<RX>(pv, cv, o);
                 float4 *dst = reinterpret_cast<float4 *>(sS1 + row * TX + xr);
 #pragma unroll
                 for (int k = 0; k < RX / 4; ++k) dst[k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
@@ -382,7 +381,9 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
             for (int k = 0; k < RY + 6; ++k) pv[k] = sS1[(yr + k) * TX + cx];
 #pragma unroll
             for (int k = 0; k < RY + 4; ++k) cv[k] = cyP[(yr + k) * TX + cx] * sy;
-            bad |= cec_run_auto<RY>(pv, cv, o);
+#pragma unroll
+            for (int k = 2; k < RY + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
+            cec_run_auto<RY>(pv, cv, o);
             const bool store = p - 3 >= sg.z0;
             const int kw = zw >= 3 ? zw - 3 : zw - 3 + I.nz;
             float *dst = I.out + (int64_t)kw * I.plane + (int64_t)(y0 + yr) * I.nx + x0 + cx;
@@ -505,7 +506,9 @@ k_cec_xyz_wide(const __grid_constant__ FastInst one, const FastInst *__restrict_
                 }
 #pragma unroll
                 for (int k = 0; k < RX + 4; ++k) cv[k] = blk[k + 2] * sx;
-                bad |= cec_run_auto<RX>(pv, cv, o);
+#pragma unroll
+                for (int k = 2; k < RX + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
+                cec_run_auto<RX>(pv, cv, o);
                 *reinterpret_cast<float4 *>(sS1 + row * TX + xr) = make_float4(o[0], o[1], o[2], o[3]);
             }
             __syncthreads();
@@ -647,7 +650,11 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
                 for (int k = 0; k < RY + 6; ++k) pv[k] = sZ[(yr + k) * PW + col];
 #pragma unroll
                 for (int k = 0; k < RY + 4; ++k) cv[k] = cyP[(yr + k) * PW + col] * sy;
-                bad |= cec_run_auto<RY>(pv, cv, o);
+                if (col >= 4 && col < TX + 4) {
+#pragma unroll
+                    for (int k = 2; k < RY + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
+                }
+                cec_run_auto<RY>(pv, cv, o);
 #pragma unroll
                 for (int i = 0; i < RY; ++i) sS2[(yr + i) * PW + col] = o[i];
             }
@@ -673,7 +680,9 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
                 }
 #pragma unroll
                 for (int k = 0; k < RX + 4; ++k) cv[k] = blk[k + 2] * sx;
-                bad |= cec_run_auto<RX>(pv, cv, o);
+#pragma unroll
+                for (int k = 2; k < RX + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
+                cec_run_auto<RX>(pv, cv, o);
                 float4 *dst = reinterpret_cast<float4 *>(I.out + (int64_t)kw * I.plane + (int64_t)(y0 + row) * I.nx +
                                                          x0 + xr);
 #pragma unroll
