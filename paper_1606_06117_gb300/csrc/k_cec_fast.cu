@@ -264,13 +264,6 @@ struct Chunks {
 };
 
 // ============================================================ order x, y, z
-#ifndef SL_NPF
-#define SL_NPF 2           // planes prefetched ahead of the one being computed
-#endif
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait_n() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
 #ifndef SL_XYZ_MINB
 #define SL_XYZ_MINB 2      // CTAs per SM the x,y,z kernel is compiled for
 #endif
@@ -288,14 +281,14 @@ __device__ __forceinline__ void cp_async_wait_n() { asm volatile("cp.async.wait_
 #endif
 
 namespace xyz {
-constexpr int TX = 32, TY = 32, NT = 256, RX = SL_XYZ_RX, RY = 4, NPF = SL_NPF, NB = NPF + 1;
+constexpr int TX = 32, TY = 32, NT = 256, RX = SL_XYZ_RX, RY = 4;
 constexpr int PH = TY + 6, PW = TX + 12;              // Phi / u_x rows [-3, TY+3), x [-4, TX+4), stride 44
 constexpr int SZ_PHI = PH * PW;
 constexpr int SZ_CY = (TY + 4) * TX;                  // u_y rows [-2, TY+2), x [0, TX)
 constexpr int SZ_CZ = TY * TX;                        // u_z rows [0, TY)
 constexpr int SLOT = 2 * SZ_PHI + SZ_CY + SZ_CZ;
 constexpr int SZ_S1 = PH * TX;                        // x-swept rows
-constexpr size_t SMEM = sizeof(float) * (NB * SLOT + SZ_S1) + 128;
+constexpr size_t SMEM = sizeof(float) * (2 * SLOT + SZ_S1) + 128;
 }  // namespace xyz
 
 template <bool BATCH>
@@ -305,7 +298,7 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
     using namespace xyz;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *buf = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float *sS1 = buf + NB * SLOT;
+    float *sS1 = buf + 2 * SLOT;
 
     const int tid = threadIdx.x;
     const FastInst *tab = BATCH ? table : &one;
@@ -329,14 +322,8 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
         chPhi.setup(tid, x0, y0, -3, -4, I.nx, I.ny);
         chCy.setup(tid, x0, y0, -2, 0, I.nx, I.ny);
         chCz.setup(tid, x0, y0, 0, 0, I.nx, I.ny);
-        // pz: plane index of the bundle, already reduced modulo nz; one commit
-        // group per plane (empty past the segment end) keeps the group count
-        // in step with the planes
-        auto issue = [&](int pz, int slot, bool real) {
-            if (!real) {
-                cp_async_commit();
-                return;
-            }
+        // pz: plane index of the bundle, already reduced modulo nz
+        auto issue = [&](int pz, int slot) {
             float *sb = buf + slot * SLOT;
             const int pz1 = pz == 0 ? I.nz - 1 : pz - 1;
             const float *vx = I.vel + (int64_t)pz * I.plane;
@@ -355,13 +342,10 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
         // p: unreduced plane; zw: p modulo nz
         auto plane = [&](auto PC, int p, int zw) {
             constexpr int P = decltype(PC)::value;
-            const int slot = (p - pfirst) % NB;
-            cp_async_wait_n<NPF - 1>();
+            const int slot = (p - pfirst) & 1;
+            cp_async_wait_all();
             __syncthreads();
-            {
-                const int zn = zw + NPF >= I.nz ? zw + NPF - I.nz : zw + NPF;
-                issue(zn, (p + NPF - pfirst) % NB, p + NPF <= plast);
-            }
+            if (p < plast) issue(zw + 1 == I.nz ? 0 : zw + 1, slot ^ 1);
             const float *sb = buf + slot * SLOT;
             const float *phiP = sb, *cxP = sb + SZ_PHI, *cyP = sb + 2 * SZ_PHI, *czP = sb + 2 * SZ_PHI + SZ_CY;
             constexpr int XR = TX / RX;
@@ -417,8 +401,7 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
         };
 
         int zw = wrapz(pfirst, I.nz);
-#pragma unroll
-        for (int j = 0; j < NPF; ++j) issue(zw + j >= I.nz ? zw + j - I.nz : zw + j, j, pfirst + j <= plast);
+        issue(zw, 0);
         for (int p = pfirst; p <= plast; p += 2) {
             plane(std::integral_constant<int, 0>(), p, zw);
             zw = zw + 1 == I.nz ? 0 : zw + 1;
@@ -569,7 +552,7 @@ k_cec_xyz_wide(const __grid_constant__ FastInst one, const FastInst *__restrict_
 
 // ============================================================ order z, y, x
 namespace zyx {
-constexpr int TX = 32, TY = 32, NT = SL_ZYX_NT, RX = SL_ZYX_RX, RY = SL_ZYX_RY, NPF = SL_NPF, NB = NPF + 1;
+constexpr int TX = 32, TY = 32, NT = SL_ZYX_NT, RX = SL_ZYX_RX, RY = SL_ZYX_RY;
 constexpr int PH = TY + 6, PW = TX + 12;
 constexpr int SZ_PHI = PH * PW;                      // Phi and u_z (plane p-1): rows [-3, TY+3)
 constexpr int SZ_CY = (TY + 4) * PW;                 // u_y (plane p-3): rows [-2, TY+2)
@@ -577,7 +560,7 @@ constexpr int SZ_CX = TY * PW;                       // u_x (plane p-3): rows [0
 constexpr int SLOT = 2 * SZ_PHI + SZ_CY + SZ_CX;
 constexpr int NZC = (TX + 6) * (TY + 6);             // z-swept columns (x, y in [-3, T+3))
 constexpr int NCOL = (NZC + NT - 1) / NT;
-constexpr size_t SMEM = sizeof(float) * (NB * SLOT + SZ_PHI + SZ_CX) + 128;
+constexpr size_t SMEM = sizeof(float) * (2 * SLOT + SZ_PHI + SZ_CX) + 128;
 }  // namespace zyx
 
 template <bool BATCH>
@@ -588,7 +571,7 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
     using namespace zyx;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *buf = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float *sZ = buf + NB * SLOT;                     // z-swept plane, rows [-3, TY+3)
+    float *sZ = buf + 2 * SLOT;                      // z-swept plane, rows [-3, TY+3)
     float *sS2 = sZ + SZ_PHI;                        // y-swept rows [0, TY)
 
     const int tid = threadIdx.x;
@@ -621,11 +604,7 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
         chCx.setup(tid, x0, y0, 0, -4, I.nx, I.ny);
 
         // pz: plane index of the bundle, already reduced modulo nz
-        auto issue = [&](int pz, int slot, bool real) {
-            if (!real) {
-                cp_async_commit();
-                return;
-            }
+        auto issue = [&](int pz, int slot) {
             float *sb = buf + slot * SLOT;
             const int nz = I.nz;
             const int pz1 = pz == 0 ? nz - 1 : pz - 1;
@@ -643,13 +622,10 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
 
         auto plane = [&](auto PC, int p, int zw) {
             constexpr int P = decltype(PC)::value;
-            const int slot = (p - pfirst) % NB;
-            cp_async_wait_n<NPF - 1>();
+            const int slot = (p - pfirst) & 1;
+            cp_async_wait_all();
             __syncthreads();
-            {
-                const int zn = zw + NPF >= I.nz ? zw + NPF - I.nz : zw + NPF;
-                issue(zn, (p + NPF - pfirst) % NB, p + NPF <= plast);
-            }
+            if (p < plast) issue(zw + 1 == I.nz ? 0 : zw + 1, slot ^ 1);
             const float *sb = buf + slot * SLOT;
             const float *phiP = sb, *czP = sb + SZ_PHI, *cyP = sb + 2 * SZ_PHI, *cxP = sb + 2 * SZ_PHI + SZ_CY;
             // ---- z sweep on the halo-widened columns
@@ -715,8 +691,7 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
         };
 
         int zw = wrapz(pfirst, I.nz);
-#pragma unroll
-        for (int j = 0; j < NPF; ++j) issue(zw + j >= I.nz ? zw + j - I.nz : zw + j, j, pfirst + j <= plast);
+        issue(zw, 0);
         for (int p = pfirst; p <= plast; p += 2) {
             plane(std::integral_constant<int, 0>(), p, zw);
             zw = zw + 1 == I.nz ? 0 : zw + 1;
