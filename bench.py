@@ -46,6 +46,21 @@ def parse():
 
 
 # ----------------------------------------------------------------- helpers
+def slowest_rank_ms(ms, world, device):
+    """Max over ranks of a per-rank elapsed time (every rank gets the result)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(cells_per_rank, steps, world, slowest_ms):
+    """Cell-updates per second of the whole job (all ranks' cells over the slowest rank's time), in G."""
+    return world * cells_per_rank * steps / (slowest_ms * 1e-3) / 1e9
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -262,12 +277,9 @@ def run_ours(args):
         if world > 1:
             dist.destroy_process_group()
         return
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = slowest_rank_ms(ms, world, dev)
     ms_step = ms_max / args.steps
-    value = world * ncell * args.steps / (ms_max * 1e-3) / 1e9
+    value = whole_job_rate(ncell, args.steps, world, ms_max)
     sl_status = sl.sl_device_status(stream)
 
     # per-launch kernel time (one launch per step) for the roofline
@@ -289,10 +301,8 @@ def run_ours(args):
         h_in, h_out = h_out, h_in
     barrier()
     el = time.perf_counter() - t0
-    te = torch.tensor([el], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * ncell * ke / float(te.item()) / 1e9, "unit": UNIT,
+    el_max = slowest_rank_ms(el * 1e3, world, dev)
+    e2e = {"value": whole_job_rate(ncell, ke, world, el_max), "unit": UNIT,
            "h2d_bytes_per_step": 16 * ncell, "d2h_bytes_per_step": 4 * ncell, "steps": ke,
            "api": "sl_advect_host (pinned host buffers; H2D, step, D2H, stream sync per step)"}
 

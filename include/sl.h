@@ -168,6 +168,15 @@ int sl_norms_static(const void *a, const void *b, int64_t n, int dtype, double *
                     void *stream);
 
 /*
+ * Failure-detection self-test of the bounded device waits: one CTA waits on an
+ * mbarrier that nothing completes, gives up after `polls` polls (1 .. 2^20),
+ * sets SL_DEV_TIMEOUT in the device status word and exits normally; the
+ * context stays usable.  Returns SL_ERR_TIMEOUT when the wait ran out as
+ * intended (synchronous).  The paper has no counterpart.
+ */
+int sl_selftest_wait_timeout(unsigned polls, void *stream);
+
+/*
  * Read and clear the device status word of the current device (SL_DEV_*
  * bits).  Synchronises the stream first.
  */

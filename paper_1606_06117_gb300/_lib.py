@@ -32,7 +32,7 @@ EXPORTS = ("sl_version", "sl_last_error", "sl_init", "sl_advect", "sl_advect_mul
            "sl_batch_step", "sl_batch_destroy", "sl_autotune", "sl_norms_static",
            "sl_corrector_param_count", "sl_corrector_create", "sl_corrector_destroy", "sl_corrector_get_params",
            "sl_corrector_set_params", "sl_corrector_add_samples", "sl_corrector_get_rows", "sl_corrector_train",
-           "sl_corrector_reset", "sl_advect_learned")
+           "sl_corrector_reset", "sl_advect_learned", "sl_selftest_wait_timeout")
 
 
 class SLError(RuntimeError):
@@ -93,6 +93,7 @@ def load(path: str | None = None):
             "sl_corrector_train": ([vp, i, i, ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(ctypes.c_float), vp], i),
             "sl_corrector_reset": ([vp], i),
             "sl_advect_learned": ([vp, vp, vp, vp, i, i64p, dp, d, i, i, d, ctypes.POINTER(i), dp, vp], i),
+            "sl_selftest_wait_timeout": ([ctypes.c_uint, vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -191,6 +192,14 @@ def sl_norms(a, b, n, dtype, stream=None):
 def sl_norms_static(a, b, n, dtype, out, stream=None):
     """Norms into the device buffer ``out`` (3 float64) with no allocation."""
     return _check(load().sl_norms_static(_ptr(a), _ptr(b), int(n), int(dtype), _ptr(out), _stream(stream)))
+
+
+def sl_selftest_wait_timeout(polls=1000, stream=None):
+    """Returns the status code (SL_ERR_TIMEOUT = -5 when the bounded wait gave up)."""
+    rc = load().sl_selftest_wait_timeout(int(polls), _stream(stream))
+    if rc not in (0, -5):
+        raise SLError(rc, load().sl_last_error().decode())
+    return rc
 
 
 def sl_device_status(stream=None):

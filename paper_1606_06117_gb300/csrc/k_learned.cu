@@ -513,6 +513,32 @@ __global__ void __launch_bounds__(MT) k_learned_step(const float *__restrict__ p
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem));
 }
 
+// Failure-detection self-test: waits on an mbarrier that no thread or copy
+// ever completes, gives up after `polls` polls like every bounded wait of the
+// library, and records SL_DEV_TIMEOUT.  Faults, traps or hangs nothing.
+__global__ void k_wait_selftest(unsigned polls, unsigned *status, unsigned *gave_up)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init1(&bar);   // expects one arrival that never comes
+    __syncthreads();
+    bool ok = false;
+    for (unsigned it = 0; it < polls && !ok; ++it) {
+        unsigned r;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(r)
+            : "r"(smem_u32(&bar)), "r"(0u)
+            : "memory");
+        ok = r != 0;
+    }
+    if (!ok && threadIdx.x == 0) {
+        atomicOr(status, 2u);
+        atomicAdd(gave_up, 1u);
+    }
+}
+
 // FP32 parameters -> the inference weight image: W1 (64 x 80, K zero-padded)
 // and W2 (64 x 64) as BF16 K-major core matrices, then b1, b2, w3, b3 in FP32.
 __global__ void k_pack(const float *__restrict__ params, unsigned char *__restrict__ wb)
@@ -712,6 +738,23 @@ int sl_corrector_train(sl_corrector *c, int iters, int batch, float lr, uint64_t
         return lfail(SL_ERR_CUDA, "training");
     if (last_loss) *last_loss = l / (float)batch;
     return SL_OK;
+}
+
+int sl_selftest_wait_timeout(unsigned polls, void *stream)
+{
+    if (polls < 1 || polls > (1u << 20)) return lfail(SL_ERR_ARG, "polls must be in [1, 2^20]");
+    DevCtx *ctx = ctx_get();
+    if (!ctx) return lfail(SL_ERR_CUDA, "no device context");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned *gave_up = ctx->counters + 255;
+    if (cudaMemsetAsync(gave_up, 0, 4, st) != cudaSuccess) return lfail(SL_ERR_CUDA, "memset");
+    k_wait_selftest<<<1, 32, 0, st>>>(polls, ctx->status, gave_up);
+    unsigned h = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&h, gave_up, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return lfail(SL_ERR_CUDA, "self-test launch");
+    return h == 1 ? SL_ERR_TIMEOUT : lfail(SL_ERR_CUDA, "the self-test wait completed unexpectedly");
 }
 
 int sl_corrector_reset(sl_corrector *c)

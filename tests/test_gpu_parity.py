@@ -272,3 +272,14 @@ def test_deformation_512_sampled_parity(parity):
         ref = oracle_at_cells(f, vel, sp, dt, "CEC", parity, cells)
         got = o[cells[:, 2], cells[:, 1], cells[:, 0]].cpu().double().numpy()
         assert rel_l2(got, ref) <= 1e-5
+
+
+def test_bounded_wait_times_out_and_reports():
+    """A device wait that nothing completes gives up, sets SL_DEV_TIMEOUT and leaves
+    the context usable (no fault, trap or hang)."""
+    sl.sl_device_status()
+    assert sl.sl_selftest_wait_timeout(2000) == -5
+    assert sl.sl_device_status() & sl.DEV_TIMEOUT
+    assert sl.sl_device_status() == 0
+    x = torch.ones(4, device=DEV)
+    assert float((x * 2).sum()) == 8.0
