@@ -75,7 +75,7 @@ def build(verbose: bool = False, extra: list[str] | None = None, jobs: int | Non
     """Compile every csrc/*.cu for sm_103a and link libsl.so; returns its path.
     ``extra`` adds nvcc flags (e.g. -D tuning constants); ``outdir`` builds a
     separate copy of the library there instead of _build/."""
-    extra = list(extra or [])
+    extra = list(extra or []) + os.environ.get("SL_NVCC_EXTRA", "").split()
     outdir = outdir or BUILD
     lib = os.path.join(outdir, "libsl.so")
     os.makedirs(outdir, exist_ok=True)
