@@ -561,8 +561,14 @@ k_cec_xyz_wide(const __grid_constant__ FastInst one, const FastInst *__restrict_
 #ifndef SL_XYZ_WS
 #define SL_XYZ_WS 0
 #endif
+#ifndef SL_WS_NA
+#define SL_WS_NA 256
+#endif
+#ifndef SL_WS_RX
+#define SL_WS_RX 8
+#endif
 namespace xws {
-constexpr int TX = 32, TY = 32, NA = 256, NBT = 256, NT = NA + NBT, RX = 8, RY = 4, NR = 2;
+constexpr int TX = 32, TY = 32, NA = SL_WS_NA, NBT = 256, NT = NA + NBT, RX = SL_WS_RX, RY = 4, NR = 2;
 constexpr int PH = TY + 6, PW = TX + 12;
 constexpr int SZ_PHI = PH * PW;
 constexpr int SZ_CY = (TY + 4) * TX;
@@ -711,13 +717,16 @@ k_cec_xyz_ws(const __grid_constant__ FastInst one, const FastInst *__restrict__ 
                 }
                 bar_named(1, NA);
                 float pv[RY + 6], cv[RY + 4], o[RY];
+                const bool ythread = tid < TX * TY / RY;
+                if (ythread) {
 #pragma unroll
-                for (int k = 0; k < RY + 6; ++k) pv[k] = sS1[(yr + k) * TX + cx];
+                    for (int k = 0; k < RY + 6; ++k) pv[k] = sS1[(yr + k) * TX + cx];
 #pragma unroll
-                for (int k = 0; k < RY + 4; ++k) cv[k] = cyP[(yr + k) * TX + cx] * sy;
+                    for (int k = 0; k < RY + 4; ++k) cv[k] = cyP[(yr + k) * TX + cx] * sy;
 #pragma unroll
-                for (int k = 2; k < RY + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
-                cec_run_auto<RY>(pv, cv, o);
+                    for (int k = 2; k < RY + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
+                    cec_run_auto<RY>(pv, cv, o);
+                }
                 // hand the y-swept plane and its u_z plane to the z warps; the
                 // decision to go on is taken by all x/y threads together
                 const int rs = seq % NR;
@@ -729,10 +738,12 @@ k_cec_xyz_ws(const __grid_constant__ FastInst one, const FastInst *__restrict__ 
                     break;
                 }
                 float *rb = ring + rs * RING;
+                if (ythread) {
 #pragma unroll
-                for (int i = 0; i < RY; ++i) {
-                    rb[(yr + i) * TX + cx] = o[i];
-                    rb[TY * TX + (yr + i) * TX + cx] = czP[(yr + i) * TX + cx];
+                    for (int i = 0; i < RY; ++i) {
+                        rb[(yr + i) * TX + cx] = o[i];
+                        rb[TY * TX + (yr + i) * TX + cx] = czP[(yr + i) * TX + cx];
+                    }
                 }
                 __syncwarp();
                 if ((tid & 31) == 0) mbar_arrive(&full[rs]);
