@@ -413,404 +413,6 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
     flag_cfl(status, bad);
 }
 
-// x,y,z order on 512 threads (two CTAs per SM when registers allow): the y
-// sweep hands its results to the z windows through shared memory, so that each
-// thread keeps only two z windows.
-#ifndef SL_XYZ_WIDE
-#define SL_XYZ_WIDE 0
-#endif
-namespace xyzw {
-constexpr int TX = 32, TY = 32, NT = 512, RX = 4, RY = 4, ZC = TX * TY / NT;
-constexpr int PH = TY + 6, PW = TX + 12;
-constexpr int SZ_PHI = PH * PW;
-constexpr int SZ_CY = (TY + 4) * TX;
-constexpr int SZ_CZ = TY * TX;
-constexpr int SLOT = 2 * SZ_PHI + SZ_CY + SZ_CZ;
-constexpr int SZ_S1 = PH * TX;
-constexpr int SZ_S2 = TY * TX;
-constexpr size_t SMEM = sizeof(float) * (2 * SLOT + SZ_S1 + SZ_S2) + 128;
-}  // namespace xyzw
-
-template <bool BATCH>
-__global__ void __launch_bounds__(xyzw::NT, 2)
-k_cec_xyz_wide(const __grid_constant__ FastInst one, const FastInst *__restrict__ table, int ninst, int64_t total,
-               unsigned *status)
-{
-    using namespace xyzw;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *buf = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float *sS1 = buf + 2 * SLOT;
-    float *sS2 = sS1 + SZ_S1;
-
-    const int tid = threadIdx.x;
-    const FastInst *tab = BATCH ? table : &one;
-    const int64_t G = gridDim.x;
-    int64_t w = total * blockIdx.x / G;
-    const int64_t wend = total * (blockIdx.x + 1) / G;
-    bool bad = false;
-    int hint = 0;
-    Seg sg;
-    const int ycx = tid % TX, yyr = (tid / TX) * RY;          // y-sweep run (threads < TX * TY / RY)
-    const int zcx = tid % TX, zy0 = (tid / TX) * ZC;          // z columns (zcx, zy0 .. zy0 + ZC)
-    Chunks<NT, PH, (TX + 8) / 4, PW> chPhi;
-    Chunks<NT, TY + 4, TX / 4, TX> chCy;
-    Chunks<NT, TY, TX / 4, TX> chCz;
-
-    while (next_seg(tab, ninst, w, wend, hint, (double)total / (double)G, sg)) {
-        const FastInst &I = tab[sg.inst];
-        const int x0 = sg.tx * TX, y0 = sg.ty * TY;
-        const float sx = I.sx, sy = I.sy, sz = I.sz;
-        const int pfirst = sg.z0 - 3, plast = sg.z1 + 2;
-        chPhi.setup(tid, x0, y0, -3, -4, I.nx, I.ny);
-        chCy.setup(tid, x0, y0, -2, 0, I.nx, I.ny);
-        chCz.setup(tid, x0, y0, 0, 0, I.nx, I.ny);
-        auto issue = [&](int pz, int slot) {
-            float *sb = buf + slot * SLOT;
-            const int pz1 = pz == 0 ? I.nz - 1 : pz - 1;
-            const float *vx = I.vel + (int64_t)pz * I.plane;
-            chPhi.issue(sb, I.in + (int64_t)pz * I.plane);
-            chPhi.issue(sb + SZ_PHI, vx);
-            chCy.issue(sb + 2 * SZ_PHI, vx + I.ncell);
-            chCz.issue(sb + 2 * SZ_PHI + SZ_CY, I.vel + 2 * I.ncell + (int64_t)pz1 * I.plane);
-            cp_async_commit();
-        };
-        ZCol win[ZC];
-#pragma unroll
-        for (int i = 0; i < ZC; ++i) win[i].init();
-
-        auto plane = [&](auto PC, int p, int zw) {
-            constexpr int P = decltype(PC)::value;
-            const int slot = (p - pfirst) & 1;
-            cp_async_wait_all();
-            __syncthreads();
-            if (p < plast) issue(zw + 1 == I.nz ? 0 : zw + 1, slot ^ 1);
-            const float *sb = buf + slot * SLOT;
-            const float *phiP = sb, *cxP = sb + SZ_PHI, *cyP = sb + 2 * SZ_PHI, *czP = sb + 2 * SZ_PHI + SZ_CY;
-            constexpr int XR = TX / RX;
-            for (int r = tid; r < PH * XR; r += NT) {
-                const int row = r / XR, xr = (r % XR) * RX;
-                const float4 *pr = reinterpret_cast<const float4 *>(phiP + row * PW + xr);
-                const float4 *cr = reinterpret_cast<const float4 *>(cxP + row * PW + xr);
-                float blk[RX + 8], pv[RX + 6], cv[RX + 4], o[RX];
-#pragma unroll
-                for (int k = 0; k < (RX + 8) / 4; ++k) {
-                    const float4 v = pr[k];
-                    blk[4 * k] = v.x; blk[4 * k + 1] = v.y; blk[4 * k + 2] = v.z; blk[4 * k + 3] = v.w;
-                }
-#pragma unroll
-                for (int k = 0; k < RX + 6; ++k) pv[k] = blk[k + 1];
-#pragma unroll
-                for (int k = 0; k < (RX + 8) / 4; ++k) {
-                    const float4 v = cr[k];
-                    blk[4 * k] = v.x; blk[4 * k + 1] = v.y; blk[4 * k + 2] = v.z; blk[4 * k + 3] = v.w;
-                }
-#pragma unroll
-                for (int k = 0; k < RX + 4; ++k) cv[k] = blk[k + 2] * sx;
-#pragma unroll
-                for (int k = 2; k < RX + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
-                cec_run_auto<RX>(pv, cv, o);
-                *reinterpret_cast<float4 *>(sS1 + row * TX + xr) = make_float4(o[0], o[1], o[2], o[3]);
-            }
-            __syncthreads();
-            if (tid < TX * TY / RY) {
-                float pv[RY + 6], cv[RY + 4], o[RY];
-#pragma unroll
-                for (int k = 0; k < RY + 6; ++k) pv[k] = sS1[(yyr + k) * TX + ycx];
-#pragma unroll
-                for (int k = 0; k < RY + 4; ++k) cv[k] = cyP[(yyr + k) * TX + ycx] * sy;
-#pragma unroll
-                for (int k = 2; k < RY + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
-                cec_run_auto<RY>(pv, cv, o);
-#pragma unroll
-                for (int i = 0; i < RY; ++i) sS2[(yyr + i) * TX + ycx] = o[i];
-            }
-            __syncthreads();
-            const bool store = p - 3 >= sg.z0;
-            const int kw = zw >= 3 ? zw - 3 : zw - 3 + I.nz;
-            float *dst = I.out + (int64_t)kw * I.plane + (int64_t)(y0 + zy0) * I.nx + x0 + zcx;
-#pragma unroll
-            for (int i = 0; i < ZC; ++i) {
-                const float c = czP[(zy0 + i) * TX + zcx] * sz;
-                bad |= fabsf(c) > 1.f;
-                const float v = win[i].push<P>(sS2[(zy0 + i) * TX + zcx], c);
-                if (store) dst[(int64_t)i * I.nx] = v;
-            }
-        };
-
-        int zw = wrapz(pfirst, I.nz);
-        issue(zw, 0);
-        for (int p = pfirst; p <= plast; p += 2) {
-            plane(std::integral_constant<int, 0>(), p, zw);
-            zw = zw + 1 == I.nz ? 0 : zw + 1;
-            if (p + 1 <= plast) plane(std::integral_constant<int, 1>(), p + 1, zw);
-            zw = zw + 1 == I.nz ? 0 : zw + 1;
-        }
-        __syncthreads();
-    }
-    flag_cfl(status, bad);
-}
-
-// ---------------------------------------------------------------------------
-// x,y,z order, warp-specialised: warps 0-7 stage the planes and run the x and y
-// sweeps, warps 8-15 run the z windows, so the two kinds of work overlap
-// instead of alternating between CTA-wide barriers.  The y-swept plane and its
-// u_z plane go to the z warps through a ring of NR shared-memory slots guarded
-// by mbarriers (full: 8 arrivals of the x/y warps, empty: 8 arrivals of the z
-// warps).  Every mbarrier wait is bounded; a wait that runs out sets
-// SL_DEV_TIMEOUT and both groups leave the work loop.
-#ifndef SL_XYZ_WS
-#define SL_XYZ_WS 0
-#endif
-#ifndef SL_WS_NA
-#define SL_WS_NA 256
-#endif
-#ifndef SL_WS_RX
-#define SL_WS_RX 8
-#endif
-namespace xws {
-constexpr int TX = 32, TY = 32, NA = SL_WS_NA, NBT = 256, NT = NA + NBT, RX = SL_WS_RX, RY = 4, NR = 2;
-constexpr int PH = TY + 6, PW = TX + 12;
-constexpr int SZ_PHI = PH * PW;
-constexpr int SZ_CY = (TY + 4) * TX;
-constexpr int SZ_CZ = TY * TX;
-constexpr int SLOT = 2 * SZ_PHI + SZ_CY + SZ_CZ;     // staged plane (x/y warps only)
-constexpr int SZ_S1 = PH * TX;
-constexpr int RING = 2 * TY * TX;                    // y-swept plane + u_z plane
-constexpr size_t SMEM = sizeof(float) * (2 * SLOT + SZ_S1 + NR * RING) + 128 + 64;
-constexpr unsigned kPolls = 1u << 22;
-}  // namespace xws
-
-__device__ __forceinline__ void mbar_init_n(uint64_t *bar, unsigned n)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(n) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_wait_polls(uint64_t *bar, unsigned parity, unsigned polls)
-{
-    for (unsigned it = 0; it < polls; ++it) {
-        unsigned ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(ok)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-__device__ __forceinline__ void bar_named(int id, int n) { asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
-// Named barrier that also returns the AND of v over the n participating threads.
-__device__ __forceinline__ bool bar_and(int id, int n, bool v)
-{
-    unsigned r;
-    asm volatile(
-        "{\n\t.reg .pred q, p;\n\t"
-        "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.and.pred p, %2, %3, q;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(r)
-        : "r"((unsigned)v), "r"(id), "r"(n)
-        : "memory");
-    return r != 0;
-}
-
-template <bool BATCH>
-__global__ void __launch_bounds__(xws::NT, 1)
-k_cec_xyz_ws(const __grid_constant__ FastInst one, const FastInst *__restrict__ table, int ninst, int64_t total,
-             unsigned *status)
-{
-    using namespace xws;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *buf = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float *sS1 = buf + 2 * SLOT;
-    float *ring = sS1 + SZ_S1;
-    uint64_t *full = reinterpret_cast<uint64_t *>(ring + NR * RING);
-    uint64_t *empty = full + NR;
-    __shared__ int s_abort;
-
-    const int tid = threadIdx.x;
-    const FastInst *tab = BATCH ? table : &one;
-    const int64_t G = gridDim.x;
-    const int64_t wbeg = total * blockIdx.x / G, wend = total * (blockIdx.x + 1) / G;
-    if (tid == 0) {
-        for (int i = 0; i < NR; ++i) {
-            mbar_init_n(&full[i], NA / 32);
-            mbar_init_n(&empty[i], NBT / 32);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        s_abort = 0;
-    }
-    __syncthreads();
-    bool bad = false;
-    const double share = (double)total / (double)G;
-
-    if (tid < NA) {
-        // ======================= x / y warps
-        Chunks<NA, PH, (TX + 8) / 4, PW> chPhi;
-        Chunks<NA, TY + 4, TX / 4, TX> chCy;
-        Chunks<NA, TY, TX / 4, TX> chCz;
-        const int cx = tid % TX, yr = (tid / TX) * RY;
-        unsigned seq = 0;          // planes handed to the ring so far
-        int64_t w = wbeg;
-        int hint = 0;
-        Seg sg;
-        bool alive = true;
-        while (alive && next_seg(tab, ninst, w, wend, hint, share, sg)) {
-            const FastInst &I = tab[sg.inst];
-            const int x0 = sg.tx * TX, y0 = sg.ty * TY;
-            const float sx = I.sx, sy = I.sy;
-            const int pfirst = sg.z0 - 3, plast = sg.z1 + 2;
-            chPhi.setup(tid, x0, y0, -3, -4, I.nx, I.ny);
-            chCy.setup(tid, x0, y0, -2, 0, I.nx, I.ny);
-            chCz.setup(tid, x0, y0, 0, 0, I.nx, I.ny);
-            auto issue = [&](int pz, int slot) {
-                float *sb = buf + slot * SLOT;
-                const int pz1 = pz == 0 ? I.nz - 1 : pz - 1;
-                const float *vx = I.vel + (int64_t)pz * I.plane;
-                chPhi.issue(sb, I.in + (int64_t)pz * I.plane);
-                chPhi.issue(sb + SZ_PHI, vx);
-                chCy.issue(sb + 2 * SZ_PHI, vx + I.ncell);
-                chCz.issue(sb + 2 * SZ_PHI + SZ_CY, I.vel + 2 * I.ncell + (int64_t)pz1 * I.plane);
-                cp_async_commit();
-            };
-            int zw = wrapz(pfirst, I.nz);
-            issue(zw, 0);
-            for (int p = pfirst; p <= plast; ++p) {
-                const int slot = (p - pfirst) & 1;
-                cp_async_wait_all();
-                bar_named(1, NA);
-                if (p < plast) issue(zw + 1 == I.nz ? 0 : zw + 1, slot ^ 1);
-                zw = zw + 1 == I.nz ? 0 : zw + 1;
-                const float *sb = buf + slot * SLOT;
-                const float *phiP = sb, *cxP = sb + SZ_PHI, *cyP = sb + 2 * SZ_PHI, *czP = sb + 2 * SZ_PHI + SZ_CY;
-                constexpr int XR = TX / RX;
-                for (int r = tid; r < PH * XR; r += NA) {
-                    const int row = r / XR, xr = (r % XR) * RX;
-                    const float4 *pr = reinterpret_cast<const float4 *>(phiP + row * PW + xr);
-                    const float4 *cr = reinterpret_cast<const float4 *>(cxP + row * PW + xr);
-                    float blk[RX + 8], pv[RX + 6], cv[RX + 4], o[RX];
-#pragma unroll
-                    for (int k = 0; k < (RX + 8) / 4; ++k) {
-                        const float4 v = pr[k];
-                        blk[4 * k] = v.x; blk[4 * k + 1] = v.y; blk[4 * k + 2] = v.z; blk[4 * k + 3] = v.w;
-                    }
-#pragma unroll
-                    for (int k = 0; k < RX + 6; ++k) pv[k] = blk[k + 1];
-#pragma unroll
-                    for (int k = 0; k < (RX + 8) / 4; ++k) {
-                        const float4 v = cr[k];
-                        blk[4 * k] = v.x; blk[4 * k + 1] = v.y; blk[4 * k + 2] = v.z; blk[4 * k + 3] = v.w;
-                    }
-#pragma unroll
-                    for (int k = 0; k < RX + 4; ++k) cv[k] = blk[k + 2] * sx;
-#pragma unroll
-                    for (int k = 2; k < RX + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
-                    cec_run_auto<RX>(pv, cv, o);
-                    float4 *dst = reinterpret_cast<float4 *>(sS1 + row * TX + xr);
-#pragma unroll
-                    for (int k = 0; k < RX / 4; ++k) dst[k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
-                }
-                bar_named(1, NA);
-                float pv[RY + 6], cv[RY + 4], o[RY];
-                const bool ythread = tid < TX * TY / RY;
-                if (ythread) {
-#pragma unroll
-                    for (int k = 0; k < RY + 6; ++k) pv[k] = sS1[(yr + k) * TX + cx];
-#pragma unroll
-                    for (int k = 0; k < RY + 4; ++k) cv[k] = cyP[(yr + k) * TX + cx] * sy;
-#pragma unroll
-                    for (int k = 2; k < RY + 2; ++k) bad |= fabsf(cv[k]) > 1.f;
-                    cec_run_auto<RY>(pv, cv, o);
-                }
-                // hand the y-swept plane and its u_z plane to the z warps; the
-                // decision to go on is taken by all x/y threads together
-                const int rs = seq % NR;
-                const unsigned ph = (seq / NR) & 1u;
-                const bool ok = seq < NR || mbar_wait_polls(&empty[rs], ph ^ 1u, kPolls);
-                if (!bar_and(1, NA, ok && s_abort == 0)) {
-                    s_abort = 1;
-                    alive = false;
-                    break;
-                }
-                float *rb = ring + rs * RING;
-                if (ythread) {
-#pragma unroll
-                    for (int i = 0; i < RY; ++i) {
-                        rb[(yr + i) * TX + cx] = o[i];
-                        rb[TY * TX + (yr + i) * TX + cx] = czP[(yr + i) * TX + cx];
-                    }
-                }
-                __syncwarp();
-                if ((tid & 31) == 0) mbar_arrive(&full[rs]);
-                ++seq;
-            }
-        }
-        cp_async_wait_all();
-    } else {
-        // ======================= z warps
-        const int t = tid - NA;
-        const int cx = t % TX, yr = (t / TX) * RY;
-        unsigned seq = 0;
-        int64_t w = wbeg;
-        int hint = 0;
-        Seg sg;
-        bool alive = true;
-        while (alive && next_seg(tab, ninst, w, wend, hint, share, sg)) {
-            const FastInst &I = tab[sg.inst];
-            const int x0 = sg.tx * TX, y0 = sg.ty * TY;
-            const float sz = I.sz;
-            const int pfirst = sg.z0 - 3, plast = sg.z1 + 2;
-            ZCol win[RY];
-#pragma unroll
-            for (int i = 0; i < RY; ++i) win[i].init();
-            int zw = wrapz(pfirst, I.nz);
-            auto plane = [&](auto PC, int p) {
-                constexpr int P = decltype(PC)::value;
-                const int rs = seq % NR;
-                const unsigned ph = (seq / NR) & 1u;
-                // the warp decides together (its lanes arrive on `empty` as one)
-                if (!__all_sync(0xffffffffu, mbar_wait_polls(&full[rs], ph, kPolls))) {
-                    s_abort = 1;
-                    alive = false;
-                    return;
-                }
-                const float *rb = ring + rs * RING;
-                float v[RY], cz[RY], res[RY];
-#pragma unroll
-                for (int i = 0; i < RY; ++i) {
-                    v[i] = rb[(yr + i) * TX + cx];
-                    cz[i] = rb[TY * TX + (yr + i) * TX + cx] * sz;
-                    bad |= fabsf(cz[i]) > 1.f;
-                }
-                __syncwarp();
-                if ((t & 31) == 0) mbar_arrive(&empty[rs]);
-                ++seq;
-                push_all<P, RY>(win, v, cz, res);
-                if (p - 3 >= sg.z0) {
-                    const int kw = zw >= 3 ? zw - 3 : zw - 3 + I.nz;
-                    float *dst = I.out + (int64_t)kw * I.plane + (int64_t)(y0 + yr) * I.nx + x0 + cx;
-#pragma unroll
-                    for (int i = 0; i < RY; ++i) dst[(int64_t)i * I.nx] = res[i];
-                }
-            };
-            for (int p = pfirst; p <= plast && alive; p += 2) {
-                plane(std::integral_constant<int, 0>(), p);
-                zw = zw + 1 == I.nz ? 0 : zw + 1;
-                if (alive && p + 1 <= plast) plane(std::integral_constant<int, 1>(), p + 1);
-                zw = zw + 1 == I.nz ? 0 : zw + 1;
-            }
-        }
-    }
-    __syncthreads();
-    if (s_abort && tid == 0) atomicOr(status, 2u);
-    flag_cfl(status, bad);
-}
-
 // ============================================================ order z, y, x
 namespace zyx {
 constexpr int TX = 32, TY = 32, NT = SL_ZYX_NT, RX = SL_ZYX_RX, RY = SL_ZYX_RY;
@@ -974,10 +576,9 @@ cudaError_t prepare(int &grid)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (cached[dev] == 0) {
-        auto kern = ZYX ? k_cec_zyx_fast<BATCH>
-                        : (SL_XYZ_WS ? k_cec_xyz_ws<BATCH> : (SL_XYZ_WIDE ? k_cec_xyz_wide<BATCH> : k_cec_xyz_fast<BATCH>));
-        const size_t smem = ZYX ? zyx::SMEM : (SL_XYZ_WS ? xws::SMEM : (SL_XYZ_WIDE ? xyzw::SMEM : xyz::SMEM));
-        const int nt = ZYX ? zyx::NT : (SL_XYZ_WS ? xws::NT : (SL_XYZ_WIDE ? xyzw::NT : xyz::NT));
+        auto kern = ZYX ? k_cec_zyx_fast<BATCH> : k_cec_xyz_fast<BATCH>;
+        const size_t smem = ZYX ? zyx::SMEM : xyz::SMEM;
+        const int nt = ZYX ? zyx::NT : xyz::NT;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0, sms = 0;
@@ -1002,10 +603,7 @@ cudaError_t go_fast(const FastInst &one, const FastInst *tab, int ninst, int64_t
     if (grid > total) grid = (int)total;
     if (ZYX)
         k_cec_zyx_fast<BATCH><<<grid, zyx::NT, zyx::SMEM, st>>>(one, tab, ninst, total, status);
-    else if (SL_XYZ_WS)
-        k_cec_xyz_ws<BATCH><<<grid, xws::NT, xws::SMEM, st>>>(one, tab, ninst, total, status);
-    else if (SL_XYZ_WIDE)
-        k_cec_xyz_wide<BATCH><<<grid, xyzw::NT, xyzw::SMEM, st>>>(one, tab, ninst, total, status);
+
     else
         k_cec_xyz_fast<BATCH><<<grid, xyz::NT, xyz::SMEM, st>>>(one, tab, ninst, total, status);
     return cudaGetLastError();
