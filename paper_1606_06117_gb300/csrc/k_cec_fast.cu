@@ -1,18 +1,25 @@
 // k_cec_fast.cu -- the fused split third-order step (SL_CEC, FP32) for grids
-// whose rows can be staged by the bulk-copy engine (nx % 4 == 0, nx >= 40,
-// ny >= 38, 16-byte aligned buffers).  Same mathematics as k_split.cu (Sec. 2
-// eqs. intro:FEC, intro:BEC, intro:CEC, intro:CECcoef, one 1D sweep per axis,
+// of whole 32 x 32 column tiles (nx, ny multiples of 32, nx >= 64, nz >= 8,
+// 16-byte aligned buffers).  Same mathematics as k_split.cu (Sec. 2 eqs.
+// intro:FEC, intro:BEC, intro:CEC, intro:CECcoef, one 1D sweep per axis,
 // Sec. 5 eqs. split:1-2), organised for instruction economy:
 //
-//  - Staging: each x-y plane of Phi and u (with its periodic halo) is copied
-//    in 16-byte cp.async chunks whose source and destination offsets every
-//    thread computes once per segment, double-buffered one plane ahead.
+//  - Staging, x,y,z order: each x-y plane bundle (the field and velocity rows
+//    a plane needs, with their periodic halo) is copied by the tensor-memory
+//    accelerator, one 2D box (cp.async.bulk.tensor) per array and row band,
+//    issued by one thread that is idle in the x phase and counted by the
+//    slot's mbarrier; two slots, so the next plane lands while this one is
+//    computed.  z,y,x order: 16-byte cp.async chunks whose source and
+//    destination offsets every thread computes once per segment (this kernel
+//    is register-bound, and per-thread copies measured faster there).
 //  - Work split: persistent CTAs; the (column tile, plane) pairs of all grids
 //    are numbered and every CTA takes one contiguous, equal share, walking
 //    z inside each column tile, so every SM gets the same number of planes.
 //  - The z sweep runs in per-column register windows (10 registers per column,
 //    the plane loop unrolled by two so no value is ever moved); the x and y
 //    sweeps run on runs of 8 / 4 cells in registers from shared memory.
+#include <cuda.h>
+#include <mutex>
 #include <type_traits>
 
 #include "sl_internal.h"
@@ -263,6 +270,76 @@ struct Chunks {
     }
 };
 
+// ------------------------------------------------------------------ staging
+// A staged array row runs from x0 - 4 to x0 + 40 (44 floats, the shared-memory
+// row stride), so the x sweeps find their halo in the row.  Its rows are
+// copied in bands [y0 - 8, y0), [y0, y0 + 32) and [y0 + 32, y0 + 32 + b): each
+// band lies within [0, ny) after the periodic wrap (ny is a multiple of 32) and
+// starts on a 128-byte boundary in shared memory.  At the periodic seam in x
+// (x0 == 0 or x0 + 32 == nx) the wide box reads zeros outside [0, nx); the four
+// columns it misses are copied by 4-wide boxes into a side buffer, which the
+// x sweep reads in their place.
+constexpr unsigned kPolls = 1u << 20;   // bound of every mbarrier wait
+
+__device__ __forceinline__ void bar_init(uint64_t *b)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(b)) : "memory");
+}
+
+// the one arrival of a slot's phase, announcing the bytes its copies deliver
+__device__ __forceinline__ void bar_arm(uint64_t *b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool bar_wait(uint64_t *b, unsigned parity, unsigned polls)
+{
+    for (unsigned it = 0; it < polls; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred q;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, q;\n\t}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(b)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// box (x, y, z) of a 3D tensor map into shared memory (128-byte aligned)
+__device__ __forceinline__ void tma3(float *dst, const CUtensorMap *m, int x, int y, int z, uint64_t *b)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_u32(dst)),
+        "l"(m), "r"(x), "r"(y), "r"(z), "r"(smem_u32(b))
+        : "memory");
+}
+
+// Tensor maps of one instance: box shapes (width x rows) over the field
+// tensor [nz][ny][nx] (P) and the velocity tensor [3 nz][ny][nx] (V).
+enum {
+    M_P44_8, M_P44_32, M_P44_3, M_P4_8, M_P4_32, M_P4_3,
+    M_V44_8, M_V44_32, M_V44_3, M_V4_8, M_V4_32, M_V4_3, M_V32_2, M_V32_32, NMAPS
+};
+struct FastMaps {
+    CUtensorMap m[NMAPS];
+};
+static_assert(sizeof(FastMaps) == kFastMapsBytes, "tensor map block size");
+
+// After a wait gave up: waits (bounded) for the phase each slot still expects,
+// so that no copy lands in shared memory after the CTA has left, and records
+// the timeout.  A slot with nothing in flight just runs out its polls.
+template <int NS>
+__device__ __forceinline__ void drain(uint64_t *bars, unsigned par, unsigned *status)
+{
+    for (int k = 0; k < NS; ++k) bar_wait(&bars[k], (par >> k) & 1u, kPolls >> 4);
+    if (threadIdx.x == 0) atomicOr(status, 2u);
+}
+
 // ============================================================ order x, y, z
 #ifndef SL_XYZ_MINB
 #define SL_XYZ_MINB 2      // CTAs per SM the x,y,z kernel is compiled for
@@ -283,17 +360,52 @@ struct Chunks {
 namespace xyz {
 constexpr int TX = 32, TY = 32, NT = 256, RX = SL_XYZ_RX, RY = 4;
 constexpr int PH = TY + 6, PW = TX + 12;              // Phi / u_x rows [-3, TY+3), x [-4, TX+4), stride 44
-constexpr int SZ_PHI = PH * PW;
-constexpr int SZ_CY = (TY + 4) * TX;                  // u_y rows [-2, TY+2), x [0, TX)
-constexpr int SZ_CZ = TY * TX;                        // u_z rows [0, TY)
-constexpr int SLOT = 2 * SZ_PHI + SZ_CY + SZ_CZ;
+// slot layout (floats; every part starts on a 128-byte boundary): Phi and u_x
+// rows [-8, TY+3) at stride PW, u_y rows [-2, TY+2) and u_z rows [0, TY) at
+// stride TX, and the seam side buffers of Phi and u_x (rows [-8, TY+3), 4 wide)
+constexpr int O_PHI = 0, O_UX = 1920, O_UY = 2 * 1920, O_UZ = O_UY + (TY + 4) * TX, O_SP = O_UZ + TY * TX,
+              O_SX = O_SP + 192, SLOT = O_SX + 192;
+static_assert(43 * PW <= 1920 && 43 * 4 <= 192 && SLOT % 32 == 0, "slot layout");
 constexpr int SZ_S1 = PH * TX;                        // x-swept rows
+constexpr unsigned BYTES = 4u * (2 * 43 * PW + (TY + 4) * TX + TY * TX), BYTES_SEAM = 4u * 2 * 43 * 4;
 constexpr size_t SMEM = sizeof(float) * (2 * SLOT + SZ_S1) + 128;
 }  // namespace xyz
 
+// Stages the bundle of plane pz (reduced modulo nz) for the x,y,z order into
+// slot sb: Phi, u_x and u_y at pz, u_z at pz - 1 (one thread).
+__device__ __forceinline__ void xyz_issue(float *sb, uint64_t *b, const CUtensorMap *m, int x0, int y0, int nx,
+                                          int ny, int nz, int pz, bool seam)
+{
+    using namespace xyz;
+    const int yt = y0 - 8 < 0 ? y0 - 8 + ny : y0 - 8, yb = y0 + TY >= ny ? y0 + TY - ny : y0 + TY;
+    const int yt2 = y0 - 2 < 0 ? y0 - 2 + ny : y0 - 2;
+    const int pz1 = pz == 0 ? nz - 1 : pz - 1;
+    bar_arm(b, BYTES + (seam ? BYTES_SEAM : 0u));
+    tma3(sb + O_PHI, &m[M_P44_8], x0 - 4, yt, pz, b);
+    tma3(sb + O_PHI + 8 * PW, &m[M_P44_32], x0 - 4, y0, pz, b);
+    tma3(sb + O_PHI + 40 * PW, &m[M_P44_3], x0 - 4, yb, pz, b);
+    tma3(sb + O_UX, &m[M_V44_8], x0 - 4, yt, pz, b);
+    tma3(sb + O_UX + 8 * PW, &m[M_V44_32], x0 - 4, y0, pz, b);
+    tma3(sb + O_UX + 40 * PW, &m[M_V44_3], x0 - 4, yb, pz, b);
+    tma3(sb + O_UY, &m[M_V32_2], x0, yt2, nz + pz, b);
+    tma3(sb + O_UY + 2 * TX, &m[M_V32_32], x0, y0, nz + pz, b);
+    tma3(sb + O_UY + 34 * TX, &m[M_V32_2], x0, yb, nz + pz, b);
+    tma3(sb + O_UZ, &m[M_V32_32], x0, y0, 2 * nz + pz1, b);
+    if (seam) {
+        const int xs = x0 == 0 ? nx - 4 : 0;
+        tma3(sb + O_SP, &m[M_P4_8], xs, yt, pz, b);
+        tma3(sb + O_SP + 32, &m[M_P4_32], xs, y0, pz, b);
+        tma3(sb + O_SP + 160, &m[M_P4_3], xs, yb, pz, b);
+        tma3(sb + O_SX, &m[M_V4_8], xs, yt, pz, b);
+        tma3(sb + O_SX + 32, &m[M_V4_32], xs, y0, pz, b);
+        tma3(sb + O_SX + 160, &m[M_V4_3], xs, yb, pz, b);
+    }
+}
+
 template <bool BATCH>
 __global__ void __launch_bounds__(xyz::NT, SL_XYZ_MINB)
-k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict__ table, int ninst, int64_t total, unsigned *status)
+k_cec_xyz_fast(const __grid_constant__ FastInst one, const __grid_constant__ FastMaps one_maps,
+               const FastInst *__restrict__ table, int ninst, int64_t total, unsigned *status)
 {
     using namespace xyz;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -309,29 +421,28 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
     int hint = 0;
     Seg sg;
     const int cx = tid % TX, yr = (tid / TX) * RY;
-    Chunks<NT, PH, (TX + 8) / 4, PW> chPhi;        // Phi and u_x: rows [-3, TY+3), x [-4, TX+4)
-    Chunks<NT, TY + 4, TX / 4, TX> chCy;           // u_y: rows [-2, TY+2), x [0, TX)
-    Chunks<NT, TY, TX / 4, TX> chCz;               // u_z: rows [0, TY)
+    __shared__ uint64_t bars[2];
+    __shared__ int gave_up;               // set when a bounded wait gave up
+    if (tid == 0) {
+        bar_init(&bars[0]);
+        bar_init(&bars[1]);
+        gave_up = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    unsigned par = 0;                     // bit k: parity of slot k's next completion
+    bool alive = true;
 
-    while (next_seg(tab, ninst, w, wend, hint, (double)total / (double)G, sg)) {
+    while (alive && next_seg(tab, ninst, w, wend, hint, (double)total / (double)G, sg)) {
         const FastInst &I = tab[sg.inst];
+        const CUtensorMap *maps = BATCH ? static_cast<const FastMaps *>(I.maps)->m : one_maps.m;
         const int x0 = sg.tx * TX, y0 = sg.ty * TY;
         const float sx = I.sx, sy = I.sy, sz = I.sz;
         const int pfirst = sg.z0 - 3, plast = sg.z1 + 2;
-
-        chPhi.setup(tid, x0, y0, -3, -4, I.nx, I.ny);
-        chCy.setup(tid, x0, y0, -2, 0, I.nx, I.ny);
-        chCz.setup(tid, x0, y0, 0, 0, I.nx, I.ny);
-        // pz: plane index of the bundle, already reduced modulo nz
-        auto issue = [&](int pz, int slot) {
-            float *sb = buf + slot * SLOT;
-            const int pz1 = pz == 0 ? I.nz - 1 : pz - 1;
-            const float *vx = I.vel + (int64_t)pz * I.plane;
-            chPhi.issue(sb, I.in + (int64_t)pz * I.plane);
-            chPhi.issue(sb + SZ_PHI, vx);
-            chCy.issue(sb + 2 * SZ_PHI, vx + I.ncell);
-            chCz.issue(sb + 2 * SZ_PHI + SZ_CY, I.vel + 2 * I.ncell + (int64_t)pz1 * I.plane);
-            cp_async_commit();
+        const bool seam = x0 == 0 || x0 + TX == I.nx;
+        // one thread, idle in the x phase, stages plane pz (reduced modulo nz) into slot sl
+        auto issue = [&](int pz, int sl) {
+            if (tid == NT - 1) xyz_issue(buf + sl * SLOT, &bars[sl], maps, x0, y0, I.nx, I.ny, I.nz, pz, seam);
         };
 
         ZCol win[RY];
@@ -340,30 +451,41 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
 
         // one plane: x sweep into sS1, y sweep, z windows, store
         // p: unreduced plane; zw: p modulo nz
-        auto plane = [&](auto PC, int p, int zw) {
+        // returns false when the wait for the plane's bundle gave up (all threads agree)
+        auto plane = [&](auto PC, int p, int zw) -> bool {
             constexpr int P = decltype(PC)::value;
             const int slot = (p - pfirst) & 1;
-            cp_async_wait_all();
-            __syncthreads();
-            if (p < plast) issue(zw + 1 == I.nz ? 0 : zw + 1, slot ^ 1);
             const float *sb = buf + slot * SLOT;
-            const float *phiP = sb, *cxP = sb + SZ_PHI, *cyP = sb + 2 * SZ_PHI, *czP = sb + 2 * SZ_PHI + SZ_CY;
-            constexpr int XR = TX / RX;
+            if (bar_wait(&bars[slot], (par >> slot) & 1u, kPolls))
+                par ^= 1u << slot;
+            else
+                gave_up = 1;
+            __syncthreads();
+            const bool stop = gave_up;   // acted on at the end of the plane (all threads agree)
+            // the other slot (plane p - 1, consumed) is refilled with plane p + 1
+            if (p < plast) issue(zw + 1 == I.nz ? 0 : zw + 1, slot ^ 1);
+            const float *phiP = sb + O_PHI + 5 * PW, *cxP = sb + O_UX + 5 * PW, *cyP = sb + O_UY, *czP = sb + O_UZ;
+            constexpr int XR = TX / RX, KB = (RX + 8) / 4;
             for (int r = tid; r < PH * XR; r += NT) {
                 const int row = r / XR, xr = (r % XR) * RX;
                 const float4 *pr = reinterpret_cast<const float4 *>(phiP + row * PW + xr);
                 const float4 *cr = reinterpret_cast<const float4 *>(cxP + row * PW + xr);
+                // at the seam the first block of the first run (x in [-4, 0)) or the
+                // last block of the last run (x in [32, 36)) is in the side buffers
+                const bool sl = seam && x0 == 0 && xr == 0, sr = seam && x0 != 0 && xr == TX - RX;
+                const float4 *sp = reinterpret_cast<const float4 *>(sb + O_SP) + row + 5;
+                const float4 *sx4 = reinterpret_cast<const float4 *>(sb + O_SX) + row + 5;
                 float blk[RX + 8], pv[RX + 6], cv[RX + 4], o[RX];
 #pragma unroll
-                for (int k = 0; k < (RX + 8) / 4; ++k) {
-                    const float4 v = pr[k];
+                for (int k = 0; k < KB; ++k) {
+                    const float4 v = *(k == 0 && sl ? sp : (k == KB - 1 && sr ? sp : pr + k));
                     blk[4 * k] = v.x; blk[4 * k + 1] = v.y; blk[4 * k + 2] = v.z; blk[4 * k + 3] = v.w;
                 }
 #pragma unroll
                 for (int k = 0; k < RX + 6; ++k) pv[k] = blk[k + 1];
 #pragma unroll
-                for (int k = 0; k < (RX + 8) / 4; ++k) {
-                    const float4 v = cr[k];
+                for (int k = 0; k < KB; ++k) {
+                    const float4 v = *(k == 0 && sl ? sx4 : (k == KB - 1 && sr ? sx4 : cr + k));
                     blk[4 * k] = v.x; blk[4 * k + 1] = v.y; blk[4 * k + 2] = v.z; blk[4 * k + 3] = v.w;
                 }
 #pragma unroll
@@ -398,15 +520,19 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const FastInst *__restrict_
 #pragma unroll
                 for (int i = 0; i < RY; ++i) dst[(int64_t)i * I.nx] = res[i];
             }
+            return !stop;
         };
 
         int zw = wrapz(pfirst, I.nz);
-        issue(zw, 0);
+        issue(zw, 0);   // the previous segment ended with a barrier
         for (int p = pfirst; p <= plast; p += 2) {
-            plane(std::integral_constant<int, 0>(), p, zw);
-            zw = zw + 1 == I.nz ? 0 : zw + 1;
-            if (p + 1 <= plast) plane(std::integral_constant<int, 1>(), p + 1, zw);
-            zw = zw + 1 == I.nz ? 0 : zw + 1;
+            if (!plane(std::integral_constant<int, 0>(), p, zw) ||
+                (p + 1 <= plast && !plane(std::integral_constant<int, 1>(), p + 1, zw + 1 == I.nz ? 0 : zw + 1))) {
+                drain<2>(bars, par, status);
+                alive = false;
+                break;
+            }
+            zw = zw + 2 >= I.nz ? zw + 2 - I.nz : zw + 2;
         }
         __syncthreads();   // shared buffers are reused by the next segment
     }
@@ -428,8 +554,8 @@ constexpr size_t SMEM = sizeof(float) * (2 * SLOT + SZ_PHI + SZ_CX) + 128;
 
 template <bool BATCH>
 __global__ void __launch_bounds__(zyx::NT, 512 / SL_ZYX_NT)
-k_cec_zyx_fast(const __grid_constant__ FastInst one, const FastInst *__restrict__ table, int ninst, int64_t total,
-               unsigned *status)
+k_cec_zyx_fast(const __grid_constant__ FastInst one, const __grid_constant__ FastMaps, const FastInst *__restrict__ table,
+               int ninst, int64_t total, unsigned *status)
 {
     using namespace zyx;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -593,8 +719,8 @@ cudaError_t prepare(int &grid)
 }
 
 template <bool ZYX, bool BATCH>
-cudaError_t go_fast(const FastInst &one, const FastInst *tab, int ninst, int64_t total, unsigned *status,
-                    int grid_req, cudaStream_t st)
+cudaError_t go_fast(const FastInst &one, const FastMaps &maps, const FastInst *tab, int ninst, int64_t total,
+                    unsigned *status, int grid_req, cudaStream_t st)
 {
     int grid = 0;
     cudaError_t e = prepare<ZYX, BATCH>(grid);
@@ -602,14 +728,101 @@ cudaError_t go_fast(const FastInst &one, const FastInst *tab, int ninst, int64_t
     if (grid_req > 0) grid = grid_req;
     if (grid > total) grid = (int)total;
     if (ZYX)
-        k_cec_zyx_fast<BATCH><<<grid, zyx::NT, zyx::SMEM, st>>>(one, tab, ninst, total, status);
-
+        k_cec_zyx_fast<BATCH><<<grid, zyx::NT, zyx::SMEM, st>>>(one, maps, tab, ninst, total, status);
     else
-        k_cec_xyz_fast<BATCH><<<grid, xyz::NT, xyz::SMEM, st>>>(one, tab, ninst, total, status);
+        k_cec_xyz_fast<BATCH><<<grid, xyz::NT, xyz::SMEM, st>>>(one, maps, tab, ninst, total, status);
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ tensor maps
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, looked up once through the runtime
+EncodeTiled encoder()
+{
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(f);
+    });
+    return fn;
+}
+
+#ifndef SL_TMA_L2
+#define SL_TMA_L2 CU_TENSOR_MAP_L2_PROMOTION_L2_256B
+#endif
+
+// Encodes the box shapes of one instance: the field f.in as [nz][ny][nx] and
+// the velocity f.vel as [3 nz][ny][nx] (FP32, row stride nx, plane stride nx ny).
+cudaError_t encode_maps(FastMaps &fm, const FastInst &f)
+{
+    EncodeTiled enc = encoder();
+    if (!enc) return cudaErrorNotSupported;
+    static const int shape[NMAPS][3] = {
+        {0, 44, 8}, {0, 44, 32}, {0, 44, 3}, {0, 4, 8}, {0, 4, 32}, {0, 4, 3},   // field
+        {1, 44, 8}, {1, 44, 32}, {1, 44, 3}, {1, 4, 8}, {1, 4, 32}, {1, 4, 3},   // velocity
+        {1, 32, 2}, {1, 32, 32}};
+    for (int k = 0; k < NMAPS; ++k) {
+        const bool v = shape[k][0] == 1;
+        const cuuint64_t dims[3] = {(cuuint64_t)f.nx, (cuuint64_t)f.ny, (cuuint64_t)f.nz * (v ? 3 : 1)};
+        const cuuint64_t strides[2] = {(cuuint64_t)f.nx * sizeof(float), (cuuint64_t)f.plane * sizeof(float)};
+        const cuuint32_t box[3] = {(cuuint32_t)shape[k][1], (cuuint32_t)shape[k][2], 1u};
+        const cuuint32_t step[3] = {1u, 1u, 1u};
+        void *base = const_cast<float *>(v ? f.vel : f.in);
+        if (enc(&fm.m[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, step,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, SL_TMA_L2,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+}
+
+// Recently encoded maps of single-instance launches, keyed by buffers and sizes.
+cudaError_t cached_maps(FastMaps &fm, const FastInst &f)
+{
+    struct Entry {
+        const float *in = nullptr, *vel = nullptr;
+        int nx = 0, ny = 0, nz = 0;
+        FastMaps maps;
+    };
+    static Entry cache[8];
+    static int next = 0;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry &c : cache)
+        if (c.in == f.in && c.vel == f.vel && c.nx == f.nx && c.ny == f.ny && c.nz == f.nz && c.in) {
+            fm = c.maps;
+            return cudaSuccess;
+        }
+    Entry &c = cache[next];
+    cudaError_t e = encode_maps(c.maps, f);
+    if (e != cudaSuccess) {
+        c.in = nullptr;
+        return e;
+    }
+    c.in = f.in;
+    c.vel = f.vel;
+    c.nx = f.nx;
+    c.ny = f.ny;
+    c.nz = f.nz;
+    next = (next + 1) % 8;
+    fm = c.maps;
+    return cudaSuccess;
+}
+
 }  // namespace
+
+cudaError_t fast_encode_maps(void *dst, const FastInst &f)
+{
+    return encode_maps(*static_cast<FastMaps *>(dst), f);
+}
 
 bool fast_eligible(const int64_t dims[3], int ndim, int dtype, bool aligned)
 {
@@ -636,17 +849,22 @@ void fast_fill(FastInst &f, const void *in, void *out, const void *vel, const in
     f.sy = (float)s[1];
     f.sz = (float)s[2];
     f.w0 = w0;
+    f.maps = nullptr;
 }
 
 cudaError_t launch_cec_fast(const FastInst &one, const FastInst *dev_table, int ninst, int64_t total, int parity,
                             unsigned *status, int grid_req, cudaStream_t st)
 {
     const bool zyx_order = parity & 1;
+    static FastMaps unused;   // batched launches read each instance's maps from the table
     if (dev_table)
-        return zyx_order ? go_fast<true, true>(one, dev_table, ninst, total, status, grid_req, st)
-                         : go_fast<false, true>(one, dev_table, ninst, total, status, grid_req, st);
-    return zyx_order ? go_fast<true, false>(one, nullptr, 1, total, status, grid_req, st)
-                     : go_fast<false, false>(one, nullptr, 1, total, status, grid_req, st);
+        return zyx_order ? go_fast<true, true>(one, unused, dev_table, ninst, total, status, grid_req, st)
+                         : go_fast<false, true>(one, unused, dev_table, ninst, total, status, grid_req, st);
+    FastMaps maps;
+    cudaError_t e = cached_maps(maps, one);
+    if (e != cudaSuccess) return e;
+    return zyx_order ? go_fast<true, false>(one, maps, nullptr, 1, total, status, grid_req, st)
+                     : go_fast<false, false>(one, maps, nullptr, 1, total, status, grid_req, st);
 }
 
 int fast_grid(int parity)

@@ -389,14 +389,27 @@ int sl_batch_create(sl_batch **out, const sl_instance *inst, int n, int scheme, 
     for (int par = 0; par < 2; ++par) b->grid[par] = std::min(total[par], c->num_sms * batched_blocks_per_sm(par));
     void *p = nullptr;
     const size_t rec_bytes = (sizeof(BatchRec) * n + 255) & ~(size_t)255;
-    if (cudaMalloc(&p, 256 + rec_bytes + sizeof(FastInst) * 2 * n) != cudaSuccess) {
+    const size_t fast_bytes = (sizeof(FastInst) * 2 * n + 255) & ~(size_t)255;
+    const size_t map_bytes = fast ? kFastMapsBytes * 2 * n : 0;
+    if (cudaMalloc(&p, 256 + rec_bytes + fast_bytes + map_bytes) != cudaSuccess) {
         delete b;
         return fail(SL_ERR_NOMEM, "device instance table");
     }
     b->counter = static_cast<unsigned *>(p);
     b->dev_recs = reinterpret_cast<BatchRec *>(static_cast<char *>(p) + 256);
     b->dev_fast = reinterpret_cast<FastInst *>(static_cast<char *>(p) + 256 + rec_bytes);
-    cudaError_t e = cudaMemcpy(b->dev_recs, recs.data(), sizeof(BatchRec) * n, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaSuccess;
+    if (fast) {
+        // tensor maps of both directions of every instance, after the tables
+        char *dev_maps = static_cast<char *>(p) + 256 + rec_bytes + fast_bytes;
+        std::vector<unsigned char> maps(map_bytes);
+        for (size_t k = 0; k < 2 * (size_t)n && e == cudaSuccess; ++k) {
+            e = fast_encode_maps(maps.data() + k * kFastMapsBytes, ftab[k]);
+            ftab[k].maps = dev_maps + k * kFastMapsBytes;
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(dev_maps, maps.data(), map_bytes, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(b->dev_recs, recs.data(), sizeof(BatchRec) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->dev_fast, ftab.data(), sizeof(FastInst) * 2 * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->counter, 0, 256);

@@ -71,7 +71,12 @@ struct FastInst {
     int64_t plane, ncell;
     float sx, sy, sz;
     int64_t w0;
+    const void *maps;   // batched tables: device address of this instance's tensor maps
 };
+// Bytes of one instance's tensor maps (14 maps of 128 bytes, 64-byte aligned).
+constexpr size_t kFastMapsBytes = 14 * 128;
+// Encodes the tensor maps of an instance into dst (host memory, kFastMapsBytes).
+cudaError_t fast_encode_maps(void *dst, const FastInst &f);
 bool fast_eligible(const int64_t dims[3], int ndim, int dtype, bool aligned);
 void fast_fill(FastInst &f, const void *in, void *out, const void *vel, const int64_t dims[3], const double s[3],
                int64_t w0);
