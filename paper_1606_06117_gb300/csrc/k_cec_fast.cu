@@ -575,12 +575,15 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
     Chunks<NT, TY + 4, (TX + 8) / 4, PW> chCy;     // u_y: rows [-2, TY+2)
     Chunks<NT, TY, (TX + 8) / 4, PW> chCx;         // u_x: rows [0, TY)
 
-    // per-thread z columns: staged offsets (row = y + 3, col = x + 4)
+    // per-thread z columns: staged offsets (row = y + 3, col = x + 4).  The
+    // columns x in [-3, TX-3) of a row go to the 32 lanes of one warp (no bank
+    // conflicts); the six columns x in [TX-3, TX+3) of every row come after.
     int zoff[NCOL];
 #pragma unroll
     for (int j = 0; j < NCOL; ++j) {
-        const int r = tid + j * NT;
-        zoff[j] = r < NZC ? (r / (TX + 6)) * PW + (r % (TX + 6)) + 1 : -1;
+        const int r = tid + j * NT, e = r - (TY + 6) * TX;
+        zoff[j] = r < (TY + 6) * TX ? (r / TX) * PW + (r % TX) + 1
+                                    : (e < (TY + 6) * 6 ? (e / 6) * PW + TX + (e % 6) + 1 : -1);
     }
 
     while (next_seg(tab, ninst, w, wend, hint, (double)total / (double)G, sg)) {
@@ -632,8 +635,11 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
             if (p - 3 < sg.z0) return;
             const int kw = zw >= 3 ? zw - 3 : zw - 3 + I.nz;
             // ---- y sweep: columns x in [-3, TX+3), rows [0, TY) -> sS2
+            // runs: columns x in [-3, TX-3) of one row group per warp, then the six
+            // columns x in [TX-3, TX+3) of every group
             for (int r = tid; r < (TX + 6) * (TY / RY); r += NT) {
-                const int col = r % (TX + 6) + 1, yr = (r / (TX + 6)) * RY;
+                const int e = r - TX * (TY / RY);
+                const int col = e < 0 ? r % TX + 1 : TX + e % 6 + 1, yr = (e < 0 ? r / TX : e / 6) * RY;
                 float pv[RY + 6], cv[RY + 4], o[RY];
 #pragma unroll
                 for (int k = 0; k < RY + 6; ++k) pv[k] = sZ[(yr + k) * PW + col];

@@ -157,6 +157,25 @@ def test_host_buffers_equal_device_path():
     assert torch.equal(out, sl.advect(phi.to(DEV), vel.to(DEV), dt, sp, "BEC", 0).cpu())
 
 
+@pytest.mark.parametrize("parity", [0, 1])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_fast_path_courant_violation_each_axis(axis, parity):
+    """The fused fast kernels flag |C| > 1 on any axis, at interior and seam cells."""
+    shape = (16, 64, 64)                       # (nz, ny, nx): takes the fast path
+    phi, vel, sp, dt = random_case(shape, seed=11, cmax=0.5)
+    sl.sl_device_status()
+    gpu_step(phi, vel, sp, dt, "CEC", parity, "f32")
+    torch.cuda.synchronize()
+    assert sl.sl_device_status() == 0
+    for (z, y, x) in [(5, 20, 37), (0, 0, 0), (15, 63, 63), (7, 31, 32)]:
+        v = vel.clone()
+        v[axis, z, y, x] = -1.5 * sp[axis] / dt
+        gpu_step(phi, v, sp, dt, "CEC", parity, "f32")
+        torch.cuda.synchronize()
+        assert sl.sl_device_status() & sl.DEV_CFL, (axis, parity, z, y, x)
+        assert sl.sl_device_status() == 0
+
+
 def test_norms_and_courant_reductions():
     shape = (30, 40, 50)
     a = torch.randn(shape, dtype=torch.float64, device=DEV)
