@@ -337,7 +337,7 @@ template <int NS>
 __device__ __forceinline__ void drain(uint64_t *bars, unsigned par, unsigned *status)
 {
     for (int k = 0; k < NS; ++k) bar_wait(&bars[k], (par >> k) & 1u, kPolls >> 4);
-    if (threadIdx.x == 0) atomicOr(status, 2u);
+    atomicOr(status, 2u);
 }
 
 // ============================================================ order x, y, z
@@ -422,18 +422,19 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
     Seg sg;
     const int cx = tid % TX, yr = (tid / TX) * RY;
     __shared__ uint64_t bars[2];
-    __shared__ int gave_up;               // set when a bounded wait gave up
     if (tid == 0) {
         bar_init(&bars[0]);
         bar_init(&bars[1]);
-        gave_up = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
     unsigned par = 0;                     // bit k: parity of slot k's next completion
-    bool alive = true;
+    // Poll budget of a wait.  Once a wait has given up, later waits poll once:
+    // the kernel then runs to its end on stale shared data (every access stays
+    // in bounds, every thread meets every barrier) and reports the timeout.
+    unsigned polls = kPolls;
 
-    while (alive && next_seg(tab, ninst, w, wend, hint, (double)total / (double)G, sg)) {
+    while (next_seg(tab, ninst, w, wend, hint, (double)total / (double)G, sg)) {
         const FastInst &I = tab[sg.inst];
         const CUtensorMap *maps = BATCH ? static_cast<const FastMaps *>(I.maps)->m : one_maps.m;
         const int x0 = sg.tx * TX, y0 = sg.ty * TY;
@@ -451,17 +452,13 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
 
         // one plane: x sweep into sS1, y sweep, z windows, store
         // p: unreduced plane; zw: p modulo nz
-        // returns false when the wait for the plane's bundle gave up (all threads agree)
-        auto plane = [&](auto PC, int p, int zw) -> bool {
+        auto plane = [&](auto PC, int p, int zw) {
             constexpr int P = decltype(PC)::value;
             const int slot = (p - pfirst) & 1;
             const float *sb = buf + slot * SLOT;
-            if (bar_wait(&bars[slot], (par >> slot) & 1u, kPolls))
-                par ^= 1u << slot;
-            else
-                gave_up = 1;
+            if (!bar_wait(&bars[slot], (par >> slot) & 1u, polls)) polls = 1;
+            par ^= 1u << slot;
             __syncthreads();
-            const bool stop = gave_up;   // acted on at the end of the plane (all threads agree)
             // the other slot (plane p - 1, consumed) is refilled with plane p + 1
             if (p < plast) issue(zw + 1 == I.nz ? 0 : zw + 1, slot ^ 1);
             const float *phiP = sb + O_PHI + 5 * PW, *cxP = sb + O_UX + 5 * PW, *cyP = sb + O_UY, *czP = sb + O_UZ;
@@ -520,22 +517,19 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
 #pragma unroll
                 for (int i = 0; i < RY; ++i) dst[(int64_t)i * I.nx] = res[i];
             }
-            return !stop;
         };
 
         int zw = wrapz(pfirst, I.nz);
         issue(zw, 0);   // the previous segment ended with a barrier
         for (int p = pfirst; p <= plast; p += 2) {
-            if (!plane(std::integral_constant<int, 0>(), p, zw) ||
-                (p + 1 <= plast && !plane(std::integral_constant<int, 1>(), p + 1, zw + 1 == I.nz ? 0 : zw + 1))) {
-                drain<2>(bars, par, status);
-                alive = false;
-                break;
-            }
-            zw = zw + 2 >= I.nz ? zw + 2 - I.nz : zw + 2;
+            plane(std::integral_constant<int, 0>(), p, zw);
+            zw = zw + 1 == I.nz ? 0 : zw + 1;
+            if (p + 1 <= plast) plane(std::integral_constant<int, 1>(), p + 1, zw);
+            zw = zw + 1 == I.nz ? 0 : zw + 1;
         }
         __syncthreads();   // shared buffers are reused by the next segment
     }
+    if (polls != kPolls) drain<2>(bars, par ^ 3u, status);   // both slots' last phases
     flag_cfl(status, bad);
 }
 
