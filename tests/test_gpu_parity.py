@@ -230,7 +230,7 @@ def test_batched_equals_single_instance_steps():
             cur = sl.advect(cur, vel, dt, sp, "CEC", k)
         result = b if 3 % 2 == 1 else a
         # this mixed batch runs the generic kernel; a single 64^3 grid takes the
-        # bulk-copy kernel, whose float arithmetic is arranged differently
+        # fast persistent kernel, whose float arithmetic is arranged differently
         assert rel_l2(result.cpu().double().numpy(), cur.cpu().double().numpy()) <= 1e-6
 
 
