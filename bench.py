@@ -30,6 +30,9 @@ METRIC = "Gcell-updates/s at fixed L2 error: plain 3rd-order vs batched/learned 
 UNIT = "Gcell/s"
 BYTES_PER_CELL = 20          # read Phi (4) + u (12), write Phi (4)
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0   # dense bf16 burst, one earlier GB300 measurement
+# tensor-core FLOPs per cell of the learned corrector: 67 -> 64 and 64 -> 64 layers
+LEARNED_TC_FLOP_PER_CELL = 2 * (67 * 64 + 64 * 64)
 
 
 def parse():
@@ -42,6 +45,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the per-scheme and batched side measurements")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed CEC steps (for ncu); prints the plain timing line")
+    ap.add_argument("--profile-learned", action="store_true",
+                    help="only warm-up and timed learned-corrector steps (untrained weights; for ncu)")
     return ap.parse_args()
 
 
@@ -87,6 +92,17 @@ def measured_hbm_peak():
         return None
     v = find(d)
     return (v, "measured") if v else (FALLBACK_HBM_GBS, "fallback")
+
+
+def measured_bf16_peak():
+    """Dense bf16 TFLOP/s (burst) from MEASURED_PEAKS.json, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+    except Exception:
+        return FALLBACK_BF16_TFLOPS, "fallback"
+    v = d.get("bf16_tflops") if isinstance(d, dict) else None
+    return (float(v), "measured") if isinstance(v, (int, float)) else (FALLBACK_BF16_TFLOPS, "fallback")
 
 
 def kernel_source_hash():
@@ -242,6 +258,19 @@ def run_ours(args):
     dims = [n, n, n]
     a, b = phi.clone(), torch.empty_like(phi)
     stream = torch.cuda.current_stream()
+    if args.profile_learned:
+        # the learned step's work does not depend on the weights' values
+        c = sl.sl_corrector_create(0)
+        try:
+            for k in range(args.warmup + args.steps):
+                sl.sl_advect_learned(c, b, a, vel, 3, dims, sp, dt, k & 1, 0, 2.0, stream)
+                a, b = b, a
+            torch.cuda.synchronize()
+        finally:
+            sl.sl_corrector_destroy(c)
+        if rank == 0:
+            print(json.dumps({"profile_learned_run": True, "steps": args.steps}), flush=True)
+        return
 
     def step(k, src, dst):
         sl.sl_advect(dst, src, vel, 3, dims, sp, dt, sl.CEC, sl.F32, k & 1, stream)
@@ -494,9 +523,14 @@ def learned_measurement(torch, sl, stream, n=256, steps=500, check_every=25):
             rt[name] = sl.sl_norms(x, phi, phi.numel(), sl.F32, stream)[2]
     finally:
         sl.sl_corrector_destroy(c)
+    peak, kind = measured_bf16_peak()
+    tflops = LEARNED_TC_FLOP_PER_CELL * n ** 3 / (ms_l * 1e-3) / 1e12
     return {"train": {"grid": [128] * 3, "rows": 4 * 6 * 100000, "iters": 3000, "batch": 4096,
                       "loss_first": loss0, "loss_last": loss, "seconds": train_s},
             "learned_gcell_s": n ** 3 / (ms_l * 1e-3) / 1e9, "learned_ms_per_step": ms_l,
+            "roofline": {"bound": "tensor", "kernel": "k_learned_step", "achieved": tflops, "peak": peak,
+                         "unit": "TFLOP/s", "frac": tflops / peak, "peak_kind": kind,
+                         "flop_per_cell": LEARNED_TC_FLOP_PER_CELL},
             "steps": steps, "check_every": check_every, "fell_back_at_step": fell_at, "checks": checks[:6],
             "roundtrip_rel_l2_100_100": rt}
 
