@@ -47,6 +47,8 @@ def parse():
                     help="only the warm-up and timed CEC steps (for ncu); prints the plain timing line")
     ap.add_argument("--profile-learned", action="store_true",
                     help="only warm-up and timed learned-corrector steps (untrained weights; for ncu)")
+    ap.add_argument("--scheme", choices=["CIR", "FEC", "BEC", "CEC"], default="CEC",
+                    help="scheme of the --profile steps")
     return ap.parse_args()
 
 
@@ -272,8 +274,10 @@ def run_ours(args):
             print(json.dumps({"profile_learned_run": True, "steps": args.steps}), flush=True)
         return
 
+    scheme = getattr(sl, args.scheme) if args.profile else sl.CEC
+
     def step(k, src, dst):
-        sl.sl_advect(dst, src, vel, 3, dims, sp, dt, sl.CEC, sl.F32, k & 1, stream)
+        sl.sl_advect(dst, src, vel, 3, dims, sp, dt, scheme, sl.F32, k & 1, stream)
 
     for k in range(args.warmup):
         step(k, a, b)
@@ -343,6 +347,8 @@ def run_ours(args):
         extras["batched_c3"] = batched_measurement(torch, sl, stream)
         torch.cuda.empty_cache()
         extras["deformation_c5"] = deformation_measurement(torch, sl, stream)
+        torch.cuda.empty_cache()
+        extras["cec_512"] = cec512_measurement(torch, sl, stream)
         torch.cuda.empty_cache()
         extras["learned_c4"] = learned_measurement(torch, sl, stream)
 
@@ -533,6 +539,25 @@ def learned_measurement(torch, sl, stream, n=256, steps=500, check_every=25):
                          "flop_per_cell": LEARNED_TC_FLOP_PER_CELL},
             "steps": steps, "check_every": check_every, "fell_back_at_step": fell_at, "checks": checks[:6],
             "roundtrip_rel_l2_100_100": rt}
+
+
+def cec512_measurement(torch, sl, stream, n=512, timed=40):
+    """One scalar field, the split CEC step on the 512^3 ABC / 32-mode workload
+    (the size the HBM-roofline target is stated for): rate, per-step time and
+    the roofline fraction of the fused kernels (20 B per cell-update)."""
+    phi, vel, sp, dt = workload(n, "cuda", torch)
+    a, b = phi, torch.empty_like(phi)
+
+    def fn(k):
+        sl.sl_advect(b, a, vel, 3, [n] * 3, sp, dt, sl.CEC, sl.F32, k & 1, stream)
+    fn(0)
+    fn(1)
+    ms = time_steps(torch, stream, fn, timed)
+    peak, kind = measured_hbm_peak()
+    gbs = BYTES_PER_CELL * n ** 3 / (ms * 1e-3) / 1e9
+    return {"grid": [n] * 3, "gcell_s": n ** 3 / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_kind": kind}}
 
 
 def deformation_measurement(torch, sl, stream, n=512, total_steps=2000, timed=20):

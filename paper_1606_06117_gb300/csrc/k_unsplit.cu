@@ -83,6 +83,43 @@ __device__ __forceinline__ void stage_rows(int tid, T *dst, const T *src, int x0
     }
 }
 
+// 16-byte chunks of the staged rows [r0, r0 + NR) x columns [-4, TX+4) of a
+// tile, when a row crosses the periodic seams at most once (nx >= TX + 8 and
+// ny >= TY + NST): thread tid owns chunks tid + k NT, whose in-plane source and
+// shared-memory offsets are computed once per tile.
+template <typename T, int NT, int TX, int NR, int PW>
+struct RowChunks {
+    static constexpr int V = 16 / sizeof(T), CPR = (TX + 8) / V, N = NR * CPR, K = (N + NT - 1) / NT;
+    int src[K];
+    int dst[K];
+
+    __device__ __forceinline__ void setup(int tid, int x0, int y0, int r0, int H, int nx, int ny)
+    {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int idx = tid + k * NT;
+            if (idx < N) {
+                const int row = idx / CPR, cc = idx - row * CPR;
+                int gy = y0 + r0 + row, gx = x0 - 4 + cc * V;
+                gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+                gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+                src[k] = gy * nx + gx;
+                dst[k] = (r0 + row + H) * PW + cc * V;
+            } else {
+                src[k] = -1;
+                dst[k] = 0;
+            }
+        }
+    }
+
+    __device__ __forceinline__ void issue(T *sdst, const T *gsrc) const
+    {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (src[k] >= 0) cp_async16(sdst + dst[k], gsrc + src[k]);
+    }
+};
+
 template <typename T, typename D, int NST, int TX, int TY, bool HAS_Z, bool VEC>
 __global__ void __launch_bounds__(256)
 k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ vel, Geo g)
@@ -108,18 +145,32 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
         const int z1 = min(z0 + g.tz, g.nz);
         const int pfirst = HAS_Z ? z0 - NST : 0;
         const int plast = HAS_Z ? z1 + NST - 1 : 0;
+        // per-tile chunk offsets when rows wrap at most once (the common case)
+        const bool once = VEC && g.nx >= TX + 8 && g.ny >= TY + NST;
+        RowChunks<T, NT, TX, TY + 2 * H, PW> chPhi;
+        RowChunks<T, NT, TX, TY + 2 * (H - 1), PW> chC;
+        if (once) {
+            chPhi.setup(tid, x0, y0, -H, H, g.nx, g.ny);
+            chC.setup(tid, x0, y0, -(H - 1), H, g.nx, g.ny);
+        }
 
         auto issue = [&](int p) {
             const int b = p - pfirst;
             const int64_t base = (int64_t)wrapi(p, g.nz) * g.plane;
-            stage_rows<T, NT, TX, PW, VEC>(tid, sPhi + (b % K::NPHI) * SLOT, in + base, x0, y0, -H, TY + 2 * H, H,
-                                           g.nx, g.ny);
             const int64_t bc = HAS_Z ? (int64_t)wrapi(p - 1, g.nz) * g.plane : base;
             T *cdst = sC + (b % K::NCS) * K::NC * SLOT;
+            if (once) {
+                chPhi.issue(sPhi + (b % K::NPHI) * SLOT, in + base);
 #pragma unroll
-            for (int d = 0; d < K::NC; ++d)
-                stage_rows<T, NT, TX, PW, VEC>(tid, cdst + d * SLOT, vel + d * g.ncell + bc, x0, y0, -(H - 1),
-                                               TY + 2 * (H - 1), H, g.nx, g.ny);
+                for (int d = 0; d < K::NC; ++d) chC.issue(cdst + d * SLOT, vel + d * g.ncell + bc);
+            } else {
+                stage_rows<T, NT, TX, PW, VEC>(tid, sPhi + (b % K::NPHI) * SLOT, in + base, x0, y0, -H, TY + 2 * H,
+                                               H, g.nx, g.ny);
+#pragma unroll
+                for (int d = 0; d < K::NC; ++d)
+                    stage_rows<T, NT, TX, PW, VEC>(tid, cdst + d * SLOT, vel + d * g.ncell + bc, x0, y0, -(H - 1),
+                                                   TY + 2 * (H - 1), H, g.nx, g.ny);
+            }
             cp_async_commit();
         };
         // ring slots of plane q
