@@ -134,15 +134,43 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
 
     const int tid = threadIdx.x;
     const D sxd = D(g.sx), syd = D(g.sy), szd = D(g.sz);
-    const int nitems = g.tiles_x * g.tiles_y * g.chunks;
     bool bad = false;
+    // Work split.  BEC (three stages; its shared memory allows two CTAs per SM):
+    // persistent CTAs; the (column tile, plane) pairs are numbered tile by tile
+    // and every CTA takes one contiguous, equal share, walking z inside each
+    // tile.  A tile's pairs are numbered from a tile-dependent plane, so that
+    // the share boundaries of all tiles fall on the same planes (neighbouring
+    // tiles are then processed at the same z and their shared halo rows stay in
+    // L2); planes are taken modulo nz.  CIR and FEC (more CTAs per SM): one
+    // (column tile, z chunk of g.tz planes) item per CTA, items over the grid.
+    constexpr bool PERSIST = NST == 3 && HAS_Z;
+    const int nzz = HAS_Z ? g.nz : 1;
+    const int64_t total = PERSIST ? (int64_t)g.tiles_x * g.tiles_y * nzz : (int64_t)g.tiles_x * g.tiles_y * g.chunks;
+    const int64_t G = gridDim.x;
+    int64_t w = PERSIST ? total * blockIdx.x / G : blockIdx.x;
+    const int64_t wend = PERSIST ? total * (blockIdx.x + 1) / G : total;
+    const double share = (double)total / (double)G;
 
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const int tx = item % g.tiles_x, rest = item / g.tiles_x;
-        const int x0 = tx * TX;
-        const int y0 = (rest % g.tiles_y) * TY;
-        const int z0 = (rest / g.tiles_y) * g.tz;
-        const int z1 = min(z0 + g.tz, g.nz);
+    while (w < wend) {
+        int t, z0, z1;
+        if constexpr (PERSIST) {
+            t = (int)(w / nzz);
+            const int64_t tile_w = (int64_t)t * nzz;
+            const int o = (int)(w - tile_w);
+            const int rot = (int)(fmod((double)tile_w, share) + 0.5) % nzz;
+            const int64_t e = wend < tile_w + nzz ? wend : tile_w + nzz;
+            z0 = o + rot;                   // in [0, 2 nz)
+            z1 = z0 + (int)(e - w);
+            w = e;
+        } else {
+            const int item = (int)w;
+            t = item % (g.tiles_x * g.tiles_y);
+            z0 = (item / (g.tiles_x * g.tiles_y)) * g.tz;
+            z1 = min(z0 + g.tz, g.nz);
+            w += G;
+        }
+        const int x0 = (t % g.tiles_x) * TX;
+        const int y0 = (t / g.tiles_x) * TY;
         const int pfirst = HAS_Z ? z0 - NST : 0;
         const int plast = HAS_Z ? z1 + NST - 1 : 0;
         // per-tile chunk offsets when rows wrap at most once (the common case)
@@ -203,7 +231,7 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
                     if constexpr (NST == 1) {
                         bad |= fabs(cx) > D(1) || fabs(cy) > D(1) || fabs(cz) > D(1);
                         const int gx = x0 + xx, gy = y0 + yy;
-                        if (gx < g.nx && gy < g.ny) out[(int64_t)q * g.plane + (int64_t)gy * g.nx + gx] = T(v);
+                        if (gx < g.nx && gy < g.ny) out[(int64_t)(q >= g.nz ? q - g.nz : q) * g.plane + (int64_t)gy * g.nx + gx] = T(v);
                     } else {
                         sl_l(q)[o] = v;
                     }
@@ -233,7 +261,7 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
                             bad |= fabs(cx) > D(1) || fabs(cy) > D(1) || fabs(cz) > D(1);
                             const int gx = x0 + xx, gy = y0 + yy;
                             if (gx < g.nx && gy < g.ny)
-                                out[(int64_t)q * g.plane + (int64_t)gy * g.nx + gx] = T(l0[o] + delta * D(0.5));
+                                out[(int64_t)(q >= g.nz ? q - g.nz : q) * g.plane + (int64_t)gy * g.nx + gx] = T(l0[o] + delta * D(0.5));
                         } else {
                             sl_p(q)[o] = T(D(phiq[o]) + delta * D(0.5));
                         }
@@ -257,7 +285,7 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
                         const T *p1 = HAS_Z ? (cz > T(0) ? sl_p(q - 1) : sl_p(q + 1)) : p0;
                         const T v = mlerp<T, HAS_Z>(p0, p1, o, ox, oy, fabs(cx), fabs(cy), fabs(cz));
                         const int gx = x0 + xx, gy = y0 + yy;
-                        if (gx < g.nx && gy < g.ny) out[(int64_t)q * g.plane + (int64_t)gy * g.nx + gx] = v;
+                        if (gx < g.nx && gy < g.ny) out[(int64_t)(q >= g.nz ? q - g.nz : q) * g.plane + (int64_t)gy * g.nx + gx] = v;
                     }
                 }
             }
@@ -272,11 +300,26 @@ cudaError_t go(Geo g, int grid, const void *in, void *out, const void *vel, cuda
 {
     using K = Cfg<T, D, NST, TX, TY, HAS_Z>;
     auto kern = k_unsplit<T, D, NST, TX, TY, HAS_Z, VEC>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::smem());
+    // shared-memory opt-in and resident CTAs per SM, once per device
+    static int per_dev[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (per_dev[dev] == 0) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::smem());
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K::NT, K::smem());
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        per_dev[dev] = sms * (per_sm > 0 ? per_sm : 1);
+    }
     g.tiles_y = (g.ny + TY - 1) / TY;
-    const int nitems = g.tiles_x * g.tiles_y * g.chunks;
-    const int gr = grid > 0 && grid < nitems ? grid : nitems;
+    const bool persist = NST == 3 && HAS_Z;
+    const int64_t total = (int64_t)g.tiles_x * g.tiles_y * (persist ? g.nz : g.chunks);
+    int gr = grid > 0 ? grid : (persist ? per_dev[dev] : (int)total);
+    if (gr > total) gr = (int)total;
     kern<<<gr, K::NT, K::smem(), st>>>(static_cast<const T *>(in), static_cast<T *>(out),
                                        static_cast<const T *>(vel), g);
     return cudaGetLastError();
