@@ -350,6 +350,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         extras["cec_512"] = cec512_measurement(torch, sl, stream)
         torch.cuda.empty_cache()
+        extras["rotation_c1"] = rotation_measurement(torch, sl, stream)
         extras["learned_c4"] = learned_measurement(torch, sl, stream)
 
     cpu = None
@@ -539,6 +540,33 @@ def learned_measurement(torch, sl, stream, n=256, steps=500, check_every=25):
                          "flop_per_cell": LEARNED_TC_FLOP_PER_CELL},
             "steps": steps, "check_every": check_every, "fell_back_at_step": fell_at, "checks": checks[:6],
             "roundtrip_rel_l2_100_100": rt}
+
+
+def rotation_measurement(torch, sl, stream, n=128):
+    """The 2D FP64 accuracy workload: a Gaussian (sigma 0.05 at (0.25, 0.5)) under
+    solid-body rotation u = 2 pi (0.5 - y, x - 0.5), CFL 0.5, one revolution
+    (805 steps at 128^2), every scheme; relative L2 and max error against the
+    exact solution (the initial field), computed on the device in FP64."""
+    from paper_1606_06117_gb300 import workloads as W
+    shape = (n, n)
+    phi0 = W.gaussian_unwrapped(shape, (0.25, 0.5), 0.05, device="cuda")
+    vel = W.rotation_velocity(shape, device="cuda")
+    dt, nsteps = W.dt_for_cfl(1.0, math.pi * n, 0.5)
+    sp = [1.0 / n, 1.0 / n, 1.0]   # the ABI takes three entries; the third is unused in 2D
+    out = {"grid": [n, n], "steps": nsteps, "dtype": "f64"}
+    for name in ("CIR", "FEC", "BEC", "CEC"):
+        code = getattr(sl, name)
+        x, y = phi0.clone(), torch.empty_like(phi0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(nsteps):
+            sl.sl_advect(y, x, vel, 2, [n, n, 1], sp, dt, code, sl.F64, k & 1, stream)
+            x, y = y, x
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        nrm = sl.sl_norms(x, phi0, phi0.numel(), sl.F64, stream)
+        out[name] = {"rel_l2": nrm[2], "linf": nrm[1], "us_per_step": el / nsteps * 1e6}
+    return out
 
 
 def cec512_measurement(torch, sl, stream, n=512, timed=40):
