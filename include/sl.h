@@ -276,7 +276,8 @@ int sl_corrector_train(sl_corrector *c, int iters, int batch, float lr, uint64_t
 int sl_corrector_reset(sl_corrector *c);
 /*
  * One step with the corrector: FP32 fields, ndim = 3, dims[0] % 32 == 0,
- * dims[1] % 4 == 0, dims[2] >= 3.  With check == 0 the learned step runs
+ * dims[1] % 4 == 0, dims[2] >= 3, in 16-byte aligned (else SL_ERR_UNSUPPORTED).
+ * With check == 0 the learned step runs
  * (or the plain SL_CEC step with step_parity once the corrector has fallen
  * back).  With check != 0 the plain SL_CEC and SL_BEC steps of the same input
  * are also computed; the learned error is ||learned - CEC|| / ||CEC|| and the

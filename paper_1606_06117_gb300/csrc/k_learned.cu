@@ -80,13 +80,26 @@ __device__ __forceinline__ void cell_features(At at, int x, int y, int z, float 
     const float g0 = e[0] + f[1] * (e[1] - e[0]);
     const float g1 = e[2] + f[1] * (e[3] - e[2]);
     m = g0 + f[2] * (g1 - g0);
-    float mx = 0.f;
+    // max |v_k - m| = max(max v - m, m - min v): rounding is monotonic, so this
+    // is exactly the largest rounded difference; four chains each for ILP
+    float hi[4] = {v[0], v[1], v[2], v[3]}, lo[4] = {v[0], v[1], v[2], v[3]};
 #pragma unroll
-    for (int k = 0; k < 64; ++k) mx = fmaxf(mx, fabsf(v[k] - m));
-    s = fmaxf(mx, 1e-30f);
+    for (int k = 4; k < 64; ++k) {
+        hi[k & 3] = fmaxf(hi[k & 3], v[k]);
+        lo[k & 3] = fminf(lo[k & 3], v[k]);
+    }
+    const float vmax = fmaxf(fmaxf(hi[0], hi[1]), fmaxf(hi[2], hi[3]));
+    const float vmin = fminf(fminf(lo[0], lo[1]), fminf(lo[2], lo[3]));
+    s = fmaxf(fmaxf(vmax - m, m - vmin), 1e-30f);
     const float inv = 1.f / s;
+    // feat = (v - m) / s as v inv - m inv, two cells' worth per packed FFMA2
+    const float2 inv2 = make_float2(inv, inv), nm2 = make_float2(-m * inv, -m * inv);
 #pragma unroll
-    for (int k = 0; k < 64; ++k) feat[k] = (v[k] - m) * inv;
+    for (int k = 0; k < 64; k += 2) {
+        const float2 r = __ffma2_rn(make_float2(v[k], v[k + 1]), inv2, nm2);
+        feat[k] = r.x;
+        feat[k + 1] = r.y;
+    }
     feat[64] = f[0] - 0.5f;
     feat[65] = f[1] - 0.5f;
     feat[66] = f[2] - 0.5f;
@@ -325,11 +338,12 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 
 constexpr int MT = 128;                      // cells per tile (MMA M)
 constexpr int BX = 32, BY = 4;               // tile = 32 x 4 cells of one plane
-constexpr int HX = BX + 4, HY = BY + 4, HZ = 5;   // staged block, halo 2
+constexpr int HX = BX + 8, HY = BY + 4, HZ = 5;   // staged block: x halo 4 (16-byte chunks), y, z halo 2
+constexpr int CPR = HX / 4;                         // 16-byte chunks per staged row
 constexpr int A1_BYTES = MT * KP1 * 2, A2_BYTES = MT * NH * 2;
 constexpr int W1_BYTES = NH * KP1 * 2, W2_BYTES = NH * NH * 2;
 constexpr int BLK_FLOATS = HX * HY * HZ;
-// layout of the dynamic shared memory (bytes); about 60 KB, so three CTAs fit
+// layout of the dynamic shared memory (bytes); about 70 KB, so three CTAs fit
 // on an SM and take 384 of its 512 tensor-memory columns
 constexpr int S_A1 = 0, S_A2 = S_A1 + A1_BYTES, S_W1 = S_A2 + A2_BYTES, S_W2 = S_W1 + W1_BYTES;
 constexpr int S_F = S_W2 + W2_BYTES;                          // FP32: b1, b2, w3, b3
@@ -389,13 +403,15 @@ __global__ void __launch_bounds__(MT) k_learned_step(const float *__restrict__ p
         const int ty_ = (int)((tt / tiles_x) % tiles_y);
         const int z_ = (int)(tt / ((int64_t)tiles_x * tiles_y));
         float *dst = blk + b * STAGE_FLOATS;
-        for (int i = tid; i < BLK_FLOATS; i += MT) {
-            const int bx = i % HX, by = (i / HX) % HY, bz = i / (HX * HY);
-            int gx = tx_ * BX - 2 + bx, gy = ty_ * BY - 2 + by, gz = z_ - 2 + bz;   // at most one period away
+        // x in [x0-4, x0+36) in 16-byte chunks: nx is a multiple of 32, so a
+        // chunk never straddles the periodic seam and every source is aligned
+        for (int i = tid; i < BLK_FLOATS / 4; i += MT) {
+            const int cx4 = i % CPR, row = i / CPR, by = row % HY, bz = row / HY;
+            int gx = tx_ * BX - 4 + 4 * cx4, gy = ty_ * BY - 2 + by, gz = z_ - 2 + bz;   // at most one period away
             gx += gx < 0 ? nx : (gx >= nx ? -nx : 0);
             gy += gy < 0 ? ny : (gy >= ny ? -ny : 0);
             gz += gz < 0 ? nz : (gz >= nz ? -nz : 0);
-            cp_async4(dst + i, phi + (int64_t)gz * plane + (int64_t)gy * nx + gx);
+            cp_async16(dst + 4 * i, phi + (int64_t)gz * plane + (int64_t)gy * nx + gx);
         }
         const int64_t cell_ = (int64_t)z_ * plane + (int64_t)(ty_ * BY + tid / BX) * nx + tx_ * BX + tid % BX;
         cp_async4(dst + BLK_FLOATS + tid, vel + cell_);
@@ -424,7 +440,7 @@ __global__ void __launch_bounds__(MT) k_learned_step(const float *__restrict__ p
                     ccz = fminf(fmaxf(cz, -1.f), 1.f);
         auto at = [&](int xx, int yy, int zz) {
             // xx, yy, zz are global indices within 2 cells of the cell
-            return sb[((zz - z + 2) * HY + (yy - y0 + 2)) * HX + (xx - x0 + 2)];
+            return sb[((zz - z + 2) * HY + (yy - y0 + 2)) * HX + (xx - x0 + 4)];
         };
         float feat[NIN], m, s;
         cell_features(at, x0 + cxl, y0 + cyl, z, ccx, ccy, ccz, feat, m, s);
@@ -464,11 +480,14 @@ __global__ void __launch_bounds__(MT) k_learned_step(const float *__restrict__ p
             for (int half = 0; half < 2; ++half) {
                 float v[32];
                 tmem_ld32(lane_base + half * 32, v);
+                const float4 *b1v = reinterpret_cast<const float4 *>(fw + half * 32);
 #pragma unroll
                 for (int kg = 0; kg < 4; ++kg) {
+                    const float4 ba = b1v[2 * kg], bb = b1v[2 * kg + 1];
+                    const float bias[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
                     float q[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) q[e] = fmaxf(v[kg * 8 + e] + fw[half * 32 + kg * 8 + e], 0.f);
+                    for (int e = 0; e < 8; ++e) q[e] = fmaxf(v[kg * 8 + e] + bias[e], 0.f);
                     uint4 pk = make_uint4(pack_bf16(q[0], q[1]), pack_bf16(q[2], q[3]), pack_bf16(q[4], q[5]),
                                           pack_bf16(q[6], q[7]));
                     *reinterpret_cast<uint4 *>(A + core_off(tid, half * 4 + kg, MT / 8)) = pk;
@@ -493,14 +512,26 @@ __global__ void __launch_bounds__(MT) k_learned_step(const float *__restrict__ p
         phase ^= 1u;
         tc_fence_after();
         // ---- epilogue 2: bias, ReLU, output layer, Phi_new = m + s y
-        float y = fw[3 * NH];
+        float2 ya01 = make_float2(fw[3 * NH], 0.f), ya23 = make_float2(0.f, 0.f);   // four accumulation chains
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             float v[32];
             tmem_ld32(lane_base + NH + half * 32, v);
+            const float4 *b2v = reinterpret_cast<const float4 *>(fw + NH + half * 32);
+            const float4 *w3v = reinterpret_cast<const float4 *>(fw + 2 * NH + half * 32);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) y += fmaxf(v[j] + fw[NH + half * 32 + j], 0.f) * fw[2 * NH + half * 32 + j];
+            for (int q = 0; q < 8; ++q) {
+                // bias and weight pairs: packed FADD2 / FFMA2, ReLU per lane
+                const float4 bb = b2v[q], ww = w3v[q];
+                float2 h01 = __fadd2_rn(make_float2(v[4 * q], v[4 * q + 1]), make_float2(bb.x, bb.y));
+                float2 h23 = __fadd2_rn(make_float2(v[4 * q + 2], v[4 * q + 3]), make_float2(bb.z, bb.w));
+                h01 = make_float2(fmaxf(h01.x, 0.f), fmaxf(h01.y, 0.f));
+                h23 = make_float2(fmaxf(h23.x, 0.f), fmaxf(h23.y, 0.f));
+                ya01 = __ffma2_rn(h01, make_float2(ww.x, ww.y), ya01);
+                ya23 = __ffma2_rn(h23, make_float2(ww.z, ww.w), ya23);
+            }
         }
+        const float y = (ya01.x + ya01.y) + (ya23.x + ya23.y);
         out[cell] = m + s * y;
         tc_fence_before();
         __syncthreads();
@@ -771,6 +802,8 @@ int sl_advect_learned(sl_corrector *c, void *out, const void *in, const void *ve
     if (!c || !out || !in || !vel || !dims || !spacing) return lfail(SL_ERR_ARG, "NULL argument");
     if (!learned_geometry_ok(ndim, dims))
         return lfail(SL_ERR_UNSUPPORTED, "learned steps need ndim = 3, dims[0] % 32 == 0, dims[1] % 4 == 0, dims[2] >= 3");
+    if (reinterpret_cast<uintptr_t>(in) % 16 != 0)
+        return lfail(SL_ERR_UNSUPPORTED, "learned steps need a 16-byte aligned input field");
     for (int d = 0; d < 3; ++d)
         if (!(spacing[d] > 0.0)) return lfail(SL_ERR_ARG, "spacing must be > 0");
     const int64_t n = dims[0] * dims[1] * dims[2];
