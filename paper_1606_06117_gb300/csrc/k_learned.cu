@@ -44,6 +44,20 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x)
     return x;
 }
 
+// three-input max / min (one instruction each on sm_100 and later)
+__device__ __forceinline__ float max3f(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // ------------------------------------------------------------- features
 // Computes the 67 inputs, the CIR value m and the scale s of one cell from a
 // periodic field; phi is read through `at(x, y, z)` (wrapped by the caller).
@@ -82,11 +96,15 @@ __device__ __forceinline__ void cell_features(At at, int x, int y, int z, float 
     m = g0 + f[2] * (g1 - g0);
     // max |v_k - m| = max(max v - m, m - min v): rounding is monotonic, so this
     // is exactly the largest rounded difference; four chains each for ILP
-    float hi[4] = {v[0], v[1], v[2], v[3]}, lo[4] = {v[0], v[1], v[2], v[3]};
+    float hi[4], lo[4];
 #pragma unroll
-    for (int k = 4; k < 64; ++k) {
-        hi[k & 3] = fmaxf(hi[k & 3], v[k]);
-        lo[k & 3] = fminf(lo[k & 3], v[k]);
+    for (int c = 0; c < 4; ++c) {   // chain c: v[c], v[c + 4], ..., v[c + 60]
+        hi[c] = lo[c] = v[c + 60];
+#pragma unroll
+        for (int k = c; k < 60; k += 8) {
+            hi[c] = max3f(hi[c], v[k], v[k + 4]);
+            lo[c] = min3f(lo[c], v[k], v[k + 4]);
+        }
     }
     const float vmax = fmaxf(fmaxf(hi[0], hi[1]), fmaxf(hi[2], hi[3]));
     const float vmin = fminf(fminf(lo[0], lo[1]), fminf(lo[2], lo[3]));
@@ -336,6 +354,15 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
+// pack_bf16(max(a, 0), max(b, 0)) in one conversion (rounding and the clamp at
+// zero commute, so the result is the same)
+__device__ __forceinline__ uint32_t pack_bf16_relu(float a, float b)
+{
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    return d;
+}
+
 constexpr int MT = 128;                      // cells per tile (MMA M)
 constexpr int BX = 32, BY = 4;               // tile = 32 x 4 cells of one plane
 constexpr int HX = BX + 8, HY = BY + 4, HZ = 5;   // staged block: x halo 4 (16-byte chunks), y, z halo 2
@@ -484,12 +511,15 @@ __global__ void __launch_bounds__(MT) k_learned_step(const float *__restrict__ p
 #pragma unroll
                 for (int kg = 0; kg < 4; ++kg) {
                     const float4 ba = b1v[2 * kg], bb = b1v[2 * kg + 1];
-                    const float bias[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-                    float q[8];
+                    const float2 bias[4] = {make_float2(ba.x, ba.y), make_float2(ba.z, ba.w), make_float2(bb.x, bb.y),
+                                            make_float2(bb.z, bb.w)};
+                    uint32_t w[4];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) q[e] = fmaxf(v[kg * 8 + e] + bias[e], 0.f);
-                    uint4 pk = make_uint4(pack_bf16(q[0], q[1]), pack_bf16(q[2], q[3]), pack_bf16(q[4], q[5]),
-                                          pack_bf16(q[6], q[7]));
+                    for (int e = 0; e < 4; ++e) {   // bias on pairs (FADD2), ReLU folded into the conversion
+                        const float2 h = __fadd2_rn(make_float2(v[kg * 8 + 2 * e], v[kg * 8 + 2 * e + 1]), bias[e]);
+                        w[e] = pack_bf16_relu(h.x, h.y);
+                    }
+                    const uint4 pk = make_uint4(w[0], w[1], w[2], w[3]);
                     *reinterpret_cast<uint4 *>(A + core_off(tid, half * 4 + kg, MT / 8)) = pk;
                 }
             }
