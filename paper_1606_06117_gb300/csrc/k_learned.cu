@@ -370,15 +370,24 @@ constexpr int CPR = HX / 4;                         // 16-byte chunks per staged
 constexpr int A1_BYTES = MT * KP1 * 2, A2_BYTES = MT * NH * 2;
 constexpr int W1_BYTES = NH * KP1 * 2, W2_BYTES = NH * NH * 2;
 constexpr int BLK_FLOATS = HX * HY * HZ;
-// layout of the dynamic shared memory (bytes); about 70 KB, so three CTAs fit
-// on an SM and take 384 of its 512 tensor-memory columns
-constexpr int S_A1 = 0, S_A2 = S_A1 + A1_BYTES, S_W1 = S_A2 + A2_BYTES, S_W2 = S_W1 + W1_BYTES;
+// layout of the dynamic shared memory (bytes); about 54 KB, so four CTAs fit on
+// an SM and take all 512 of its tensor-memory columns.  The layer-2 operand A2
+// reuses A1's space: layer 1's MMA has finished reading A1 (its commit was
+// waited for) before epilogue 1 writes A2, and layer 2's MMA has finished
+// before the next tile's features are written to A1.
+constexpr int CTAS_PER_SM = 4;
+static_assert(CTAS_PER_SM * 128 <= 512, "tensor-memory columns of the resident CTAs");
+static_assert(A2_BYTES <= A1_BYTES, "A2 fits in A1's space");
+constexpr int S_A1 = 0, S_A2 = S_A1, S_W1 = S_A1 + A1_BYTES, S_W2 = S_W1 + W1_BYTES;
 constexpr int S_F = S_W2 + W2_BYTES;                          // FP32: b1, b2, w3, b3
 constexpr int STAGE_FLOATS = BLK_FLOATS + 3 * MT;              // Phi block + the tile's three u components
 constexpr int S_BLK = S_F + 4 * (3 * NH + 4);                  // two stages (double buffer)
 constexpr int S_BAR = S_BLK + 2 * 4 * STAGE_FLOATS;
 constexpr int S_TM = S_BAR + 16;
 constexpr int SMEM_BYTES = S_TM + 16;
+// a fifth resident CTA would wait forever for tensor-memory columns; its shared
+// memory (with the 1 KB per-CTA reserve) cannot fit in the SM's 228 KB
+static_assert((CTAS_PER_SM + 1) * (SMEM_BYTES + 1024) > 228 * 1024, "at most CTAS_PER_SM resident CTAs");
 
 // One learned step over the grid; persistent CTAs of 128 threads (4 warps),
 // one cell per thread per tile.  wb points at the BF16 operand images of W1
@@ -848,10 +857,13 @@ int sl_advect_learned(sl_corrector *c, void *out, const void *in, const void *ve
         if (!smem_set[ctx->device]) {
             if (cudaFuncSetAttribute(k_learned_step, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess)
                 return cudaErrorInvalidValue;
+            // all of the SM's unified L1 / shared memory as shared, so four CTAs fit
+            if (cudaFuncSetAttribute(k_learned_step, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+                return cudaErrorInvalidValue;
             smem_set[ctx->device] = 1;
         }
         const int64_t tiles = (dims[0] / BX) * (dims[1] / BY) * dims[2];
-        int grid = ctx->num_sms * 3;
+        int grid = ctx->num_sms * CTAS_PER_SM;   // never more: each CTA holds 128 TMEM columns
         if (grid > tiles) grid = (int)tiles;
         k_learned_step<<<grid, MT, SMEM_BYTES, st>>>(
             static_cast<const float *>(in), static_cast<float *>(dst), static_cast<const float *>(vel), (int)dims[0],
