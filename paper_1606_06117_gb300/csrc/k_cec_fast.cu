@@ -164,23 +164,25 @@ struct ZCol {
         dl[P] = dn2;
         return out;
     }
-
-    template <int P>
-    __device__ __forceinline__ bool sign_pos(float cn) const { return cn > 0.f && c[0] > 0.f && c[1] > 0.f; }
-    template <int P>
-    __device__ __forceinline__ bool sign_neg(float cn) const { return cn < 0.f && c[0] < 0.f && c[1] < 0.f; }
 };
 
-// Pushes one plane into N windows, sign-specialised when the whole warp agrees.
+// Pushes one plane into N windows, sign-specialised when the whole warp agrees
+// that the Courant numbers at p-1, p-2 and p-3 of all its windows share a sign.
+// The two earlier planes' verdicts are carried as history bits: hist bit 0 / 1
+// = all Courant numbers of the previous push > 0 / < 0, bits 2 / 3 the same
+// one push earlier (zero at the start of a segment, like the windows' c).
 template <int P, int N>
-__device__ __forceinline__ void push_all(ZCol (&win)[N], const float (&phi)[N], const float (&cn)[N], float (&out)[N])
+__device__ __forceinline__ void push_all_h(ZCol (&win)[N], const float (&phi)[N], const float (&cn)[N],
+                                           float (&out)[N], unsigned &hist)
 {
-    bool pos = true, neg = true;
+    bool pn = true, nn = true;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        pos &= win[i].template sign_pos<P>(cn[i]);
-        neg &= win[i].template sign_neg<P>(cn[i]);
+        pn &= cn[i] > 0.f;
+        nn &= cn[i] < 0.f;
     }
+    const bool pos = pn && (hist & 5u) == 5u, neg = nn && (hist & 10u) == 10u;
+    hist = ((hist & 3u) << 2) | (pn ? 1u : 0u) | (nn ? 2u : 0u);
     const unsigned am = __activemask();
     if (__all_sync(am, pos)) {
 #pragma unroll
@@ -449,6 +451,7 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
         ZCol win[RY];
 #pragma unroll
         for (int i = 0; i < RY; ++i) win[i].init();
+        unsigned zhist = 0;
 
         // one plane: x sweep into sS1, y sweep, z windows, store
         // p: unreduced plane; zw: p modulo nz
@@ -512,7 +515,7 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
                 cz[i] = czP[(yr + i) * TX + cx] * sz;
                 bad |= fabsf(cz[i]) > 1.f;
             }
-            push_all<P, RY>(win, o, cz, res);
+            push_all_h<P, RY>(win, o, cz, res, zhist);
             if (store) {
 #pragma unroll
                 for (int i = 0; i < RY; ++i) dst[(int64_t)i * I.nx] = res[i];
