@@ -44,7 +44,8 @@ struct Cfg {
     static constexpr int NT = 256;
     static constexpr int H = NST;                          // Phi halo
     static constexpr int HW = TX + 8;                      // staged x in [-4, TX+4)
-    static constexpr int PW = HW + (sizeof(T) == 4 ? 4 : 2);
+    // row stride; FP32 BEC rows are unpadded so that three CTAs fit on an SM
+    static constexpr int PW = HW + (sizeof(T) == 4 ? (NST == 3 ? 0 : 4) : 2);
     static constexpr int PH = TY + 2 * H;                  // staged y in [-H, TY+H)
     static constexpr int SLOT = PH * PW;
     static constexpr int NPHI = HAS_Z ? 4 : 1;             // Phi ring: planes p-2..p + prefetch
@@ -52,9 +53,19 @@ struct Cfg {
     static constexpr int NC = HAS_Z ? 3 : 2;               // velocity components
     static constexpr int NL = NST >= 2 ? (HAS_Z ? 3 : 1) : 0;   // L_U[Phi] ring (type D)
     static constexpr int NP = NST >= 3 ? (HAS_Z ? 3 : 1) : 0;   // Psi ring
+    // The other rings hold only the rows they use: u rows [-(H-1), TY+H-1),
+    // L_U[Phi] (stage 1 output) rows [-(NST-1), TY+NST-1), Psi (stage 2 output)
+    // rows [-(NST-2), TY+NST-2).  Their ring pointers are shifted back by the
+    // missing top rows (SHC, SHL, SHP), so that one offset o = (y + H) PW + x + 4
+    // addresses the same cell in every ring.
+    static constexpr int SHC = 1, SHL = H - (NST - 1), SHP = H - (NST - 2);
+    static constexpr int SC = (TY + 2 * (H - 1)) * PW;
+    static constexpr int SLL = (TY + 2 * (NST - 1)) * PW;
+    static constexpr int SLP = NST >= 2 ? (TY + 2 * (NST - 2)) * PW : 0;
     static constexpr size_t smem()
     {
-        return sizeof(T) * (size_t)SLOT * (NPHI + NCS * NC + NP) + sizeof(D) * (size_t)SLOT * NL;
+        return sizeof(T) * ((size_t)SLOT * NPHI + (size_t)SC * NCS * NC + (size_t)SLP * NP) +
+               sizeof(D) * (size_t)SLL * NL;
     }
 };
 
@@ -127,10 +138,11 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
     using K = Cfg<T, D, NST, TX, TY, HAS_Z>;
     constexpr int NT = K::NT, H = K::H, PW = K::PW, SLOT = K::SLOT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int SC = K::SC, SLL = K::SLL, SLP = K::SLP;
     T *sPhi = reinterpret_cast<T *>(smem_raw);                 // [NPHI][SLOT]
-    T *sC = sPhi + K::NPHI * SLOT;                             // [NCS][NC][SLOT]
-    T *sP = sC + K::NCS * K::NC * SLOT;                        // [NP][SLOT]
-    D *sL = reinterpret_cast<D *>(sP + K::NP * SLOT);          // [NL][SLOT]
+    T *sC = sPhi + K::NPHI * SLOT;                             // [NCS][NC][SC]
+    T *sP = sC + K::NCS * K::NC * SC;                          // [NP][SLP]
+    D *sL = reinterpret_cast<D *>(sP + K::NP * SLP);           // [NL][SLL]
 
     const int tid = threadIdx.x;
     const D sxd = D(g.sx), syd = D(g.sy), szd = D(g.sz);
@@ -186,26 +198,26 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
             const int b = p - pfirst;
             const int64_t base = (int64_t)wrapi(p, g.nz) * g.plane;
             const int64_t bc = HAS_Z ? (int64_t)wrapi(p - 1, g.nz) * g.plane : base;
-            T *cdst = sC + (b % K::NCS) * K::NC * SLOT;
+            T *cdst = sC + (b % K::NCS) * K::NC * SC - K::SHC * PW;
             if (once) {
                 chPhi.issue(sPhi + (b % K::NPHI) * SLOT, in + base);
 #pragma unroll
-                for (int d = 0; d < K::NC; ++d) chC.issue(cdst + d * SLOT, vel + d * g.ncell + bc);
+                for (int d = 0; d < K::NC; ++d) chC.issue(cdst + d * SC, vel + d * g.ncell + bc);
             } else {
                 stage_rows<T, NT, TX, PW, VEC>(tid, sPhi + (b % K::NPHI) * SLOT, in + base, x0, y0, -H, TY + 2 * H,
                                                H, g.nx, g.ny);
 #pragma unroll
                 for (int d = 0; d < K::NC; ++d)
-                    stage_rows<T, NT, TX, PW, VEC>(tid, cdst + d * SLOT, vel + d * g.ncell + bc, x0, y0, -(H - 1),
+                    stage_rows<T, NT, TX, PW, VEC>(tid, cdst + d * SC, vel + d * g.ncell + bc, x0, y0, -(H - 1),
                                                    TY + 2 * (H - 1), H, g.nx, g.ny);
             }
             cp_async_commit();
         };
         // ring slots of plane q
         auto sl_phi = [&](int q) { return sPhi + ((q - pfirst) % K::NPHI) * SLOT; };
-        auto sl_c = [&](int q) { return sC + ((q + 1 - pfirst) % K::NCS) * K::NC * SLOT; };
-        auto sl_l = [&](int q) { return sL + (K::NL > 1 ? ((q + 1 - pfirst) % 3) : 0) * SLOT; };
-        auto sl_p = [&](int q) { return sP + (K::NP > 1 ? ((q + 1 - pfirst) % 3) : 0) * SLOT; };
+        auto sl_c = [&](int q) { return sC + ((q + 1 - pfirst) % K::NCS) * K::NC * SC - K::SHC * PW; };
+        auto sl_l = [&](int q) { return sL + (K::NL > 1 ? ((q + 1 - pfirst) % 3) : 0) * SLL - K::SHL * PW; };
+        auto sl_p = [&](int q) { return sP + (K::NP > 1 ? ((q + 1 - pfirst) % 3) : 0) * SLP - K::SHP * PW; };
 
         issue(pfirst);
         for (int p = pfirst; p <= plast; ++p) {
@@ -223,8 +235,8 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
                 for (int r = tid; r < RW * RH; r += NT) {
                     const int yy = r / RW, xx = r - (r / RW) * RW;
                     const int o = (yy - h + H) * PW + (xx - h + 4);
-                    const D cx = D(cP[o]) * sxd, cy = D(cP[SLOT + o]) * syd;
-                    const D cz = HAS_Z ? D(cP[2 * SLOT + o]) * szd : D(0);
+                    const D cx = D(cP[o]) * sxd, cy = D(cP[SC + o]) * syd;
+                    const D cz = HAS_Z ? D(cP[2 * SC + o]) * szd : D(0);
                     const int ox = cx > D(0) ? -1 : 1, oy = cy > D(0) ? -PW : PW;
                     const T *phi1 = HAS_Z ? (cz > D(0) ? sl_phi(q - 1) : sl_phi(q + 1)) : phi0;
                     const D v = mlerp<D, HAS_Z>(phi0, phi1, o, ox, oy, fabs(cx), fabs(cy), fabs(cz));
@@ -250,8 +262,8 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
                     for (int r = tid; r < RW * RH; r += NT) {
                         const int yy = r / RW, xx = r - (r / RW) * RW;
                         const int o = (yy - h + H) * PW + (xx - h + 4);
-                        const D cx = D(cP[o]) * sxd, cy = D(cP[SLOT + o]) * syd;
-                        const D cz = HAS_Z ? D(cP[2 * SLOT + o]) * szd : D(0);
+                        const D cx = D(cP[o]) * sxd, cy = D(cP[SC + o]) * syd;
+                        const D cz = HAS_Z ? D(cP[2 * SC + o]) * szd : D(0);
                         // reversed flow: departure x + u dt, corners toward +s
                         const int ox = cx > D(0) ? 1 : -1, oy = cy > D(0) ? PW : -PW;
                         const D *l1 = HAS_Z ? (cz > D(0) ? sl_l(q + 1) : sl_l(q - 1)) : l0;
@@ -278,8 +290,8 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
                     for (int r = tid; r < TX * TY; r += NT) {
                         const int yy = r / TX, xx = r - (r / TX) * TX;
                         const int o = (yy + H) * PW + (xx + 4);
-                        const T cx = T(D(cP[o]) * sxd), cy = T(D(cP[SLOT + o]) * syd);
-                        const T cz = HAS_Z ? T(D(cP[2 * SLOT + o]) * szd) : T(0);
+                        const T cx = T(D(cP[o]) * sxd), cy = T(D(cP[SC + o]) * syd);
+                        const T cz = HAS_Z ? T(D(cP[2 * SC + o]) * szd) : T(0);
                         bad |= fabs(cx) > T(1) || fabs(cy) > T(1) || fabs(cz) > T(1);
                         const int ox = cx > T(0) ? -1 : 1, oy = cy > T(0) ? -PW : PW;
                         const T *p1 = HAS_Z ? (cz > T(0) ? sl_p(q - 1) : sl_p(q + 1)) : p0;
@@ -308,6 +320,7 @@ cudaError_t go(Geo g, int grid, const void *in, void *out, const void *vel, cuda
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (per_dev[dev] == 0) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::smem());
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         int per_sm = 0, sms = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K::NT, K::smem());

@@ -181,5 +181,12 @@ def test_learned_rejects_unsupported_grids():
         with pytest.raises(sl.SLError) as e:
             sl.sl_advect_learned(c, torch.empty_like(a), a, v, 3, [8, 8, 8], [1, 1, 1], 0.1)
         assert e.value.code == -6
+        # a supported shape whose input does not start on a 16-byte boundary
+        base = torch.zeros(3 * 4 * 32 + 1, device=DEV)
+        shifted = base[1:].view(3, 4, 32)
+        v2 = torch.zeros(3, 3, 4, 32, device=DEV)
+        with pytest.raises(sl.SLError) as e:
+            sl.sl_advect_learned(c, torch.empty(3, 4, 32, device=DEV), shifted, v2, 3, [32, 4, 3], [1, 1, 1], 0.1)
+        assert e.value.code == -6 and "aligned" in str(e.value)
     finally:
         sl.sl_corrector_destroy(c)
