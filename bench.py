@@ -337,7 +337,8 @@ def run_ours(args):
     el_max = slowest_rank_ms(el * 1e3, world, dev)
     e2e = {"value": whole_job_rate(ncell, ke, world, el_max), "unit": UNIT,
            "h2d_bytes_per_step": 16 * ncell, "d2h_bytes_per_step": 4 * ncell, "steps": ke,
-           "api": "sl_advect_host (pinned host buffers; H2D, step, D2H, stream sync per step)"}
+           "api": "sl_advect_host (pinned host buffers; every step copies phi and u in, steps and copies phi "
+                  "back in 8 z slabs on three streams, and returns once the result is on the host)"}
 
     extras = {}
     if not args.no_extras and rank == 0:

@@ -115,10 +115,21 @@ int sl_advect_multi(void *const *outs, const void *const *ins, int nfields,
 
 /*
  * sl_advect on HOST buffers: copies in and vel to the device, runs the step
- * and copies the result back into out, then synchronises the stream.  The
- * library keeps a device staging buffer per device that grows to the largest
- * request (freed by sl_release_host_staging).  Host buffers may be pageable;
- * page-locked buffers copy faster.
+ * and copies the result back into out; returns once out holds the result.
+ * The library keeps a device staging buffer per device that grows to the
+ * largest request (freed by sl_release_host_staging); calls on one device run
+ * one at a time.  Host buffers may be pageable; page-locked buffers copy
+ * faster.
+ * Work order: the work runs after everything already queued on stream.  An
+ * SL_CEC step in FP32 on the fast geometry (whole 32 x 32 column tiles,
+ * nx >= 64, ndim = 3) with nz >= 64 is cut into z slabs of at least 32
+ * planes (at most 8 slabs) on three library-owned streams: a slab's kernel
+ * starts once the input planes it reads are on the device, and its output
+ * planes are copied back while later slabs' inputs are still being copied
+ * in.  The result equals sl_advect's bit for bit.  Other steps run on stream:
+ * copy in, step, copy back.
+ * Errors: those of sl_advect; SL_ERR_NOMEM (staging).  Every copy and kernel
+ * of the call has ended when it returns, also after an error.
  */
 int sl_advect_host(void *out, const void *in, const void *vel, int ndim,
                    const int64_t dims[3], const double spacing[3], double dt,

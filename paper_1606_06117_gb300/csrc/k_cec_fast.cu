@@ -201,30 +201,33 @@ struct Seg {
     int inst, tx, ty, z0, z1;
 };
 
-// Walks a CTA's share [w, wend) of the numbered (column tile, plane) pairs.
-// The pairs of one column tile are numbered from a tile-dependent plane phi
-// (periodic in z), chosen so that the share boundaries of every tile fall on
-// the same planes: CTAs that start together then process the same z plane of
-// neighbouring tiles at about the same time, and the halo rows one tile stages
-// are still in L2 when its neighbours stage them.
+// Walks a CTA's share [w, wend) of the numbered (column tile, plane) pairs;
+// an instance numbers the output planes [zb, zb + nzr) of each column tile.
+// Over all nz planes, the pairs of one column tile are numbered from a
+// tile-dependent plane phi (periodic in z), chosen so that the share
+// boundaries of every tile fall on the same planes: CTAs that start together
+// then process the same z plane of neighbouring tiles at about the same time,
+// and the halo rows one tile stages are still in L2 when its neighbours stage
+// them.  A partial range is numbered from zb and never wraps.
 __device__ __forceinline__ bool next_seg(const FastInst *tab, int ninst, int64_t &w, int64_t wend, int &hint,
                                          double share, Seg &s)
 {
     if (w >= wend) return false;
     while (hint + 1 < ninst && tab[hint + 1].w0 <= w) ++hint;
     const FastInst &I = tab[hint];
+    const int nzr = I.nzr;
     const int64_t local = w - I.w0;
-    const int t = (int)(local / I.nz);
-    const int o = (int)(local - (int64_t)t * I.nz);
-    const int64_t tile_w = I.w0 + (int64_t)t * I.nz;
-    int phi = (int)(fmod((double)tile_w, share) + 0.5);
-    phi = phi % I.nz;
-    const int64_t tile_end = tile_w + I.nz;
+    const int t = (int)(local / nzr);
+    const int o = (int)(local - (int64_t)t * nzr);
+    const int64_t tile_w = I.w0 + (int64_t)t * nzr;
+    int phi = 0;
+    if (nzr == I.nz) phi = (int)(fmod((double)tile_w, share) + 0.5) % I.nz;
+    const int64_t tile_end = tile_w + nzr;
     const int64_t e = wend < tile_end ? wend : tile_end;
     s.inst = hint;
     s.tx = t % I.tiles_x;
     s.ty = t / I.tiles_x;
-    s.z0 = o + phi;                    // in [0, 2 nz); planes are taken modulo nz
+    s.z0 = I.zb + o + phi;             // in [0, 2 nz); planes are taken modulo nz
     s.z1 = s.z0 + (int)(e - w);
     w = e;
     return true;
@@ -853,6 +856,8 @@ void fast_fill(FastInst &f, const void *in, void *out, const void *vel, const in
     f.sz = (float)s[2];
     f.w0 = w0;
     f.maps = nullptr;
+    f.zb = 0;
+    f.nzr = f.nz;
 }
 
 cudaError_t launch_cec_fast(const FastInst &one, const FastInst *dev_table, int ninst, int64_t total, int parity,

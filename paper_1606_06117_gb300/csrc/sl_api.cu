@@ -28,6 +28,54 @@ struct Staging {
     size_t bytes = 0;
 };
 Staging g_stage[kMaxDev];
+std::mutex g_host_mu[kMaxDev];   // host-buffer steps of one device share its staging buffer
+
+// z slabs of a host-buffer step: each slab's inputs are copied in, its planes
+// stepped and its output copied back on three streams, so that the copies of
+// later slabs overlap the kernels and read-back of earlier ones.
+constexpr int kMaxSlabs = 8;
+constexpr int64_t kMinSlabPlanes = 32;
+struct HostPipe {
+    bool ready = false;
+    cudaStream_t in = nullptr, run = nullptr, back = nullptr;
+    cudaEvent_t start = nullptr, copied[kMaxSlabs] = {}, stepped[kMaxSlabs] = {};
+    int64_t max_pitch = 0;   // largest row pitch of a 2D copy
+};
+HostPipe g_pipe[kMaxDev];
+
+void pipe_destroy(HostPipe &p)
+{
+    for (cudaStream_t *s : {&p.in, &p.run, &p.back})
+        if (*s) cudaStreamDestroy(*s);
+    if (p.start) cudaEventDestroy(p.start);
+    for (int k = 0; k < kMaxSlabs; ++k) {
+        if (p.copied[k]) cudaEventDestroy(p.copied[k]);
+        if (p.stepped[k]) cudaEventDestroy(p.stepped[k]);
+    }
+    p = HostPipe();
+}
+
+bool pipe_ready(HostPipe &p)
+{
+    if (p.ready) return true;
+    bool ok = true;
+    for (cudaStream_t *s : {&p.in, &p.run, &p.back})
+        ok = ok && cudaStreamCreateWithFlags(s, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < kMaxSlabs; ++k)
+        ok = cudaEventCreateWithFlags(&p.copied[k], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p.stepped[k], cudaEventDisableTiming) == cudaSuccess;
+    int dev = 0, pitch = 0;
+    ok = ok && cudaGetDevice(&dev) == cudaSuccess &&
+         cudaDeviceGetAttribute(&pitch, cudaDevAttrMaxPitch, dev) == cudaSuccess;
+    if (!ok) {
+        pipe_destroy(p);
+        return false;
+    }
+    p.max_pitch = pitch;
+    p.ready = true;
+    return true;
+}
 
 // autotuned launch shape per (nx, ny, nz, dtype): z chunk of the generic
 // kernels and CTA count of the fast persistent CEC kernel
@@ -226,32 +274,104 @@ int sl_advect_host(void *out, const void *in, const void *vel, int ndim, const i
     if (overlap(out, fb, in, fb) || overlap(out, fb, vel, fb * ndim)) return fail(SL_ERR_ALIAS, "out overlaps an input");
     DevCtx *c = ctx_get();
     if (!c) return fail(SL_ERR_CUDA, "could not create the device context");
+    std::lock_guard<std::mutex> hold(g_host_mu[c->device]);
     const size_t need = fb * (2 + ndim) + 512;
     Staging &sg = g_stage[c->device];
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (sg.bytes < need) {
-            if (sg.buf) cudaFree(sg.buf);
-            sg.buf = nullptr;
-            sg.bytes = 0;
-            if (cudaMalloc(&sg.buf, need) != cudaSuccess) return fail(SL_ERR_NOMEM, "device staging of %zu bytes", need);
-            sg.bytes = need;
-        }
+    if (sg.bytes < need) {
+        if (sg.buf) cudaFree(sg.buf);
+        sg.buf = nullptr;
+        sg.bytes = 0;
+        if (cudaMalloc(&sg.buf, need) != cudaSuccess) return fail(SL_ERR_NOMEM, "device staging of %zu bytes", need);
+        sg.bytes = need;
     }
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     char *base = static_cast<char *>(sg.buf);
-    void *d_in = base;
-    void *d_out = base + al(fb);
-    void *d_vel = base + 2 * al(fb);
+    char *d_in = base;
+    char *d_out = base + al(fb);
+    char *d_vel = base + 2 * al(fb);
+    const char *h_in = static_cast<const char *>(in), *h_vel = static_cast<const char *>(vel);
+    char *h_out = static_cast<char *>(out);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemcpyAsync(d_in, in, fb, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_vel, vel, fb * ndim, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
-    rc = launch_step(d_out, d_in, d_vel, ndim, dims, s, scheme, dtype, step_parity, st, c);
-    if (rc) return rc;
-    e = cudaMemcpyAsync(out, d_out, fb, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
+
+    const int64_t nz = dims[2];
+    const int nslab = (int)std::min<int64_t>(kMaxSlabs, nz / kMinSlabPlanes);
+    HostPipe &pp = g_pipe[c->device];
+    if (scheme != SL_CEC || nslab < 2 || !fast_eligible(dims, ndim, dtype, true) || !pipe_ready(pp)) {
+        // one stream: copy in, step, copy back
+        cudaError_t e = cudaMemcpyAsync(d_in, in, fb, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_vel, vel, fb * ndim, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
+        rc = launch_step(d_out, d_in, d_vel, ndim, dims, s, scheme, dtype, step_parity, st, c);
+        if (rc) return rc;
+        e = cudaMemcpyAsync(out, d_out, fb, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
+        return SL_OK;
+    }
+
+    // Slab k writes the output planes [zk, zk+1) and reads the input planes
+    // [zk - 6, zk+1 + 3) modulo nz.  The input copies run in z order, starting
+    // with the six top planes that slab 0 reads across the periodic boundary;
+    // slab k's kernel waits for the copy that completes its planes, and its
+    // read-back waits for its kernel.  Slabs hold at least 32 planes, so every
+    // copy range below is well ordered.
+    const size_t pb = (size_t)dims[0] * (size_t)dims[1] * sizeof(float);
+    auto zk = [&](int k) { return nz * k / nslab; };
+    // planes [p0, p1) of the field, then of the velocity components: one 2D
+    // copy of ndim rows (pitch fb) where fb is a valid pitch (fewer, larger
+    // copies; each copy costs a few microseconds), else one copy per component
+    auto put = [&](int64_t p0, int64_t p1) {
+        cudaError_t e = cudaSuccess;
+        if (p1 <= p0) return e;
+        const size_t off = (size_t)p0 * pb, n = (size_t)(p1 - p0) * pb;
+        e = cudaMemcpyAsync(d_in + off, h_in + off, n, cudaMemcpyHostToDevice, pp.in);
+        if (e != cudaSuccess) return e;
+        if ((int64_t)fb <= pp.max_pitch)
+            return cudaMemcpy2DAsync(d_vel + off, fb, h_vel + off, fb, n, ndim, cudaMemcpyHostToDevice, pp.in);
+        for (int d = 0; d < ndim && e == cudaSuccess; ++d)
+            e = cudaMemcpyAsync(d_vel + d * fb + off, h_vel + d * fb + off, n, cudaMemcpyHostToDevice, pp.in);
+        return e;
+    };
+    cudaError_t e = cudaEventRecord(pp.start, st);
+    for (cudaStream_t q : {pp.in, pp.run, pp.back})
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(q, pp.start, 0);
+    const char *what = "host to device copy";
+    for (int k = 0; k < nslab && e == cudaSuccess; ++k) {
+        const int64_t a = zk(k), b = zk(k + 1), top = nz - kFastHaloBelow;
+        if (k == 0) {
+            e = put(top, nz);
+            if (e == cudaSuccess) e = put(0, std::min(b + kFastHaloAbove, top));
+        } else {
+            e = put(a + kFastHaloAbove, k + 1 < nslab ? b + kFastHaloAbove : top);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(pp.copied[k], pp.in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(pp.run, pp.copied[k], 0);
+        if (e != cudaSuccess) break;
+        FastInst one;
+        fast_fill(one, d_in, d_out, d_vel, dims, s, 0);
+        one.zb = (int)a;
+        one.nzr = (int)(b - a);
+        e = launch_cec_fast(one, nullptr, 1, (int64_t)one.ntiles * one.nzr, step_parity, c->status, 0, pp.run);
+        if (e != cudaSuccess) {
+            what = "kernel launch";
+            break;
+        }
+        e = cudaEventRecord(pp.stepped[k], pp.run);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(pp.back, pp.stepped[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_out + (size_t)a * pb, d_out + (size_t)a * pb, (size_t)(b - a) * pb,
+                                cudaMemcpyDeviceToHost, pp.back);
+        if (e != cudaSuccess) what = "device to host copy";
+    }
+    // every stream is drained before returning, also after a failed call
+    for (cudaStream_t q : {pp.in, pp.run, pp.back}) {
+        const cudaError_t f = cudaStreamSynchronize(q);
+        if (e == cudaSuccess && f != cudaSuccess) {
+            e = f;
+            what = "host-buffer step";
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, what);
     return SL_OK;
 }
 
@@ -259,7 +379,7 @@ int sl_release_host_staging(void)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return fail(SL_ERR_CUDA, "no device");
-    std::lock_guard<std::mutex> lk(g_mu);
+    std::lock_guard<std::mutex> hold(g_host_mu[dev]);
     if (g_stage[dev].buf) cudaFree(g_stage[dev].buf);
     g_stage[dev] = Staging();
     return SL_OK;

@@ -61,7 +61,9 @@ cudaError_t launch_batched_cec(const BatchRec *dev_recs, int ninst, int nitems, 
 int default_tz(int dtype, int ndim, const int64_t dims[3]);
 
 // Fast FP32 CEC path (k_cec_fast.cu): one periodic grid of whole 32 x 32 column
-// tiles; w0 numbers its first (column tile, plane) pair in a batch.
+// tiles; w0 numbers its first (column tile, plane) pair in a batch.  A launch
+// writes the output planes [zb, zb + nzr) (fast_fill: all nz planes) and reads
+// the input planes [zb - 6, zb + nzr + 3), taken modulo nz.
 struct FastInst {
     const float *in;
     float *out;
@@ -72,7 +74,10 @@ struct FastInst {
     float sx, sy, sz;
     int64_t w0;
     const void *maps;   // batched tables: device address of this instance's tensor maps
+    int zb, nzr;        // output planes [zb, zb + nzr); 0 <= zb, 1 <= nzr, zb + nzr <= nz
 };
+// Input planes a fast launch reads below and above its output planes.
+constexpr int kFastHaloBelow = 6, kFastHaloAbove = 3;
 // Bytes of one instance's tensor maps (14 maps of 128 bytes, 64-byte aligned).
 constexpr size_t kFastMapsBytes = 14 * 128;
 // Encodes the tensor maps of an instance into dst (host memory, kFastMapsBytes).

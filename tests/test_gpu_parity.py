@@ -158,6 +158,46 @@ def test_host_buffers_equal_device_path():
 
 
 @pytest.mark.parametrize("parity", [0, 1])
+@pytest.mark.parametrize("shape", [(64, 32, 64), (96, 64, 64), (263, 32, 64), (40, 32, 64)])
+def test_host_buffers_in_z_slabs_equal_device_path(shape, parity):
+    """A CEC step on host buffers over the fast geometry runs in z slabs (2, 3
+    and 8 slabs, the last with slabs of 32 and 33 planes; nz = 40 runs in one
+    piece).  Each slab reads the input planes its halo reaches across slab
+    edges and across the periodic boundary.  A step on other inputs of the same
+    shape runs first, so a plane copied late or not at all leaves a stale value
+    in the device staging buffer.  The result equals the device-buffer step
+    bit for bit."""
+    phi, vel, sp, dt = random_case(shape, seed=70 + shape[0], cmax=0.9)
+    dims = [shape[2], shape[1], shape[0]]
+    other = torch.randn(shape).pin_memory()
+    junk = torch.empty(shape).pin_memory()
+    sl.sl_advect_host(junk, other, (vel.flip(1) * 0.5).contiguous().pin_memory(), 3, dims, sp, dt,
+                      sl.CEC, sl.F32, parity)
+    out = torch.empty(shape).pin_memory()
+    sl.sl_device_status()
+    sl.sl_advect_host(out, phi.pin_memory(), vel.pin_memory(), 3, dims, sp, dt, sl.CEC, sl.F32, parity)
+    assert sl.sl_device_status() == 0
+    assert torch.equal(out, sl.advect(phi.to(DEV), vel.to(DEV), dt, sp, "CEC", parity).cpu())
+    if shape[0] == 96 and parity == 0:
+        assert rel_l2(out.double().numpy(), oracle_step(phi, vel, sp, dt, "CEC", 0)) <= TOL["f32"]
+
+
+def test_host_buffers_in_z_slabs_flag_courant_violations():
+    """A violation in any slab, including the cells next to slab edges, sets
+    the status bit of a host-buffer step."""
+    shape = (96, 32, 64)
+    phi, vel, sp, dt = random_case(shape, seed=81, cmax=0.5)
+    dims = [shape[2], shape[1], shape[0]]
+    out = torch.empty(shape).pin_memory()
+    for z in (0, 31, 32, 95):
+        v = vel.clone()
+        v[2, z, 5, 7] = 1.5 * sp[2] / dt
+        sl.sl_device_status()
+        sl.sl_advect_host(out, phi.pin_memory(), v.pin_memory(), 3, dims, sp, dt, sl.CEC, sl.F32, z & 1)
+        assert sl.sl_device_status() & sl.DEV_CFL, z
+
+
+@pytest.mark.parametrize("parity", [0, 1])
 @pytest.mark.parametrize("axis", [0, 1, 2])
 def test_fast_path_courant_violation_each_axis(axis, parity):
     """The fused fast kernels flag |C| > 1 on any axis, at interior and seam cells."""
