@@ -41,3 +41,39 @@ def test_two_rank_timing_takes_the_slowest_rank():
     for rank, slow, rate in res:
         assert slow == 20.0
         assert rate == pytest.approx(2 * 1000 * 5 / 0.020 / 1e9)
+
+
+def test_oracle_replicas_on_threads_agree_with_one_oracle_call():
+    """The CPU baseline runs one oracle replica per core on threads; every
+    replica's state after two steps equals the oracle run alone on the same
+    input (the oracle keeps no shared state between calls)."""
+    import numpy as np
+
+    import bench
+    from oracle import oracle as O
+    r = bench.OracleReplicas(12, 3)
+    p0, c = r.p[0].copy(), r.c
+    r.step()
+    r.step()
+    r.close()
+    ref = O.step(O.step(p0, c, O.CEC, 0), c, O.CEC, 1)
+    for p in r.p:
+        assert np.array_equal(p, ref)
+
+
+def test_reference_arm_prints_one_line_with_its_core_count():
+    import json
+    import subprocess
+    import sys
+
+    import bench
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1"], capture_output=True, text=True, timeout=300, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0
+    assert d["cpu_baseline"]["cores"] == bench.host_cores()
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
