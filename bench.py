@@ -395,6 +395,7 @@ def run_ours(args):
         extras["cec_512"] = cec512_measurement(torch, sl, stream)
         torch.cuda.empty_cache()
         extras["rotation_c1"] = rotation_measurement(torch, sl, stream)
+        extras["resolution_f1"] = resolution_measurement(torch, sl, stream)
         extras["learned_c4"] = learned_measurement(torch, sl, stream)
 
     cpu = None
@@ -615,6 +616,61 @@ def rotation_measurement(torch, sl, stream, n=128):
         el = time.perf_counter() - t0
         nrm = sl.sl_norms(x, phi0, phi0.numel(), sl.F64, stream)
         out[name] = {"rel_l2": nrm[2], "linf": nrm[1], "us_per_step": el / nsteps * 1e6}
+    return out
+
+
+# Leading modified-equation coefficients of Table 1 for the first harmonic on
+# the unit interval (u = 1, dt = U dx), written as c * u dx^(alpha - 1) with
+# alpha the derivative order: decay of CIR (alpha 2), FEC / BEC / CEC (alpha 4),
+# phase drift of FEC / BEC (alpha 3; CEC has no third-derivative term).
+TABLE1_DECAY = {"CIR": (2, lambda U: (1 - U) / 2), "FEC": (4, lambda U: 3 * (1 - U * U) * U / 24),
+                "BEC": (4, lambda U: 9 * (1 - U) ** 2 * U / 24),
+                "CEC": (4, lambda U: (1 + U) * (1 - U) * (2 - U) / 24)}
+TABLE1_DRIFT = {"FEC": lambda U: (1 - U * U) / 6, "BEC": lambda U: (1 - U) * (1 - 2 * U) / 6}
+
+
+def resolution_measurement(torch, sl, stream, U=0.37, sizes=(64, 128, 256, 512)):
+    """The App. B resolution study on the GPU: the first harmonic cos(2 pi x) on
+    n cells along x (n x 32 x 8 grid, FP64), constant Courant number U along x.
+    One step of cos and of sin gives the amplification g; the decay rate is
+    sigma = -ln|g| / dt and the phase drift w = (arg g + U th) / dt.  Reported per
+    scheme: sigma N^(alpha - 1) per N (constant when C_alpha ~ N^(1 - alpha)), the
+    fitted exponent of sigma (1 - alpha), and the fitted coefficient at the
+    largest N over Table 1's (decay; and phase drift for FEC, BEC)."""
+    import numpy as np
+    out = {"U": U, "sizes": list(sizes), "dtype": "f64", "axis": "x"}
+    for name in ("CIR", "FEC", "BEC", "CEC"):
+        code = getattr(sl, name)
+        alpha, c_dec = TABLE1_DECAY[name]
+        sig, drift = [], []
+        for n in sizes:
+            shape = (8, 32, n)
+            th = 2 * math.pi / n
+            j = torch.arange(n, dtype=torch.float64, device="cuda") * th
+            cos = torch.cos(j).expand(shape).contiguous()
+            sin = torch.sin(j).expand(shape).contiguous()
+            vel = torch.zeros((3,) + shape, dtype=torch.float64, device="cuda")
+            vel[0] = U
+            a, b = torch.empty_like(cos), torch.empty_like(sin)
+            sl.sl_advect(a, cos, vel, 3, [n, 32, 8], [1.0, 1.0, 1.0], 1.0, code, sl.F64, 0, stream)
+            sl.sl_advect(b, sin, vel, 3, [n, 32, 8], [1.0, 1.0, 1.0], 1.0, code, sl.F64, 0, stream)
+            torch.cuda.synchronize()
+            z = torch.complex(a, b) * torch.exp(-1j * j)
+            g = complex(z.mean().item())
+            dt = U / n
+            lg = complex(np.log(g))
+            sig.append(-lg.real / dt)
+            drift.append((lg.imag + U * th) / dt)
+        k, dx = 2 * math.pi, 1.0 / sizes[-1]
+        rec = {"sigma_times_N^(alpha-1)": [s_ * n ** (alpha - 1) for s_, n in zip(sig, sizes)],
+               "alpha": alpha,
+               "fitted_exponent": float(np.polyfit(np.log(sizes), np.log(sig), 1)[0]),
+               "decay_coeff_over_table1": sig[-1] / (k ** alpha * dx ** (alpha - 1)) / c_dec(U)}
+        if name in TABLE1_DRIFT:
+            rec["drift_coeff_over_table1"] = drift[-1] / (k ** 3 * dx ** 2) / TABLE1_DRIFT[name](U)
+        else:
+            rec["drift_over_decay"] = drift[-1] / sig[-1]
+        out[name] = rec
     return out
 
 

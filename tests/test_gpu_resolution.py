@@ -1,0 +1,125 @@
+"""The App. B resolution study, run through the CUDA path: a single Fourier mode
+advected at constant velocity, whose one-step amplification the GPU step must
+reproduce.  Everything is compared against the paper's closed forms, not the
+oracle:
+
+- the one-step amplification factors of Sec. 3 (xi_F and xi_B as printed, xi_C
+  in the reading recorded in tests/golden/paper_1d_constant_u.json) and the
+  upwind symbol of the CIR update of Sec. 3, along each axis of the 3D kernels;
+- the leading modified-equation coefficients of Table 1 (decay from the even,
+  phase drift from the odd coefficients), with the App. B scaling
+  C_alpha ~ N^(1 - alpha) at fixed CFL (eq. coefres).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1606_06117_gb300 import _lib as sl
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_1d_constant_u.json")))
+SCHEMES = ["CIR", "FEC", "BEC", "CEC"]
+ALPHA = {"CIR": 2, "FEC": 4, "BEC": 4, "CEC": 4}       # leading dissipative derivative (Table 1)
+
+
+def ev(expr, **kw):
+    env = {"cos": np.cos, "sin": np.sin, "exp": np.exp}
+    env.update(kw)
+    return eval(expr, env)  # noqa: S307 - committed fixture
+
+
+def closed_form(name, U, th):
+    """One-step amplification of exp(i j th) for u > 0 (Sec. 3)."""
+    if name == "CIR":                      # (1 - U) Phi_i + U Phi_{i-1}
+        return 1 - U + U * np.exp(-1j * th)
+    af = GOLD["amplification_factors"]
+    return ev(af[{"FEC": "FEC", "BEC": "BEC", "CEC": "CEC_reading"}[name]]["expr"], U=U, th=th)
+
+
+def mode_grid(axis, n):
+    """(nz, ny, nx) with n cells along axis; the other sizes keep FP32 CEC on its
+    fast kernels (whole 32 x 32 column tiles)."""
+    shape = {0: [8, 32, n], 1: [8, n, 64], 2: [n, 32, 64]}[axis]
+    return tuple(shape)
+
+
+def gpu_symbol(name, U, k, axis, n, dtype, parity=0):
+    """One-step amplification of mode k (of n cells along axis) by the CUDA step:
+    the step of cos and of sin, projected on exp(i j th).  Returns (g, U as the
+    kernel sees it)."""
+    t = torch.float64 if dtype == "f64" else torch.float32
+    shape = mode_grid(axis, n)
+    th = 2 * math.pi * k / n
+    j = np.arange(n, dtype=np.float64) * th
+    bshape = [1, 1, 1]
+    bshape[2 - axis] = n
+    cos = torch.from_numpy(np.cos(j).reshape(bshape)).to(t).expand(shape).contiguous()
+    sin = torch.from_numpy(np.sin(j).reshape(bshape)).to(t).expand(shape).contiguous()
+    vel = torch.zeros((3,) + shape, dtype=t)
+    vel[axis] = U
+    u_eff = float(vel[axis].flatten()[0])
+    v = vel.to(DEV)
+    a = sl.advect(cos.to(DEV), v, 1.0, [1.0, 1.0, 1.0], name, parity).double().cpu().numpy()
+    b = sl.advect(sin.to(DEV), v, 1.0, [1.0, 1.0, 1.0], name, parity).double().cpu().numpy()
+    ph = np.exp(-1j * j).reshape(bshape)
+    g = ((a + 1j * b) * ph).mean()
+    return g, u_eff
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-13), ("f32", 2e-6)])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("name", SCHEMES)
+def test_one_step_amplification_matches_the_paper(name, axis, dtype, tol):
+    parities = (0, 1) if name == "CEC" else (0,)
+    for parity in parities:
+        for U in (0.2, 0.37, 0.8):
+            for k in (1, 3, 7):
+                g, u = gpu_symbol(name, U, k, axis, 64, dtype, parity)
+                want = closed_form(name, u, 2 * math.pi * k / 64)
+                assert abs(g - want) < tol, (name, axis, dtype, parity, U, k, g, want)
+
+
+def rates(name, U, n):
+    """Measured decay rate sigma and phase-drift rate w of the first harmonic on
+    the unit interval (dx = 1/n, u = 1, dt = U dx), FP64 GPU step along x."""
+    g, u = gpu_symbol(name, U, 1, 0, n, "f64")
+    dt = U / n
+    lg = np.log(g)
+    return -lg.real / dt, (lg.imag + U * 2 * math.pi / n) / dt
+
+
+def table1_rates(name, U, n):
+    """Decay and phase-drift rates of the first harmonic from Table 1's leading
+    modified-equation coefficients: d Phi / dt + u d Phi / dx = sum C_a d^a Phi / dx^a."""
+    me = GOLD["modified_equation"][name]
+    dx, u = 1.0 / n, 1.0
+    dt = U * dx / u
+    k = 2 * math.pi
+    r = sum(ev(e, U=U, u=u, dx=dx, dt=dt) * (1j * k) ** int(a) for a, e in me.items())
+    return -r.real, r.imag
+
+
+@pytest.mark.parametrize("name", SCHEMES)
+def test_resolution_study_matches_table1(name):
+    """At fixed CFL the decay rate times N^(alpha - 1) is constant (App. B), its
+    value is Table 1's coefficient, and FEC / BEC drift in phase at Table 1's
+    third-order rate; the fitted exponent of the decay is 1 - alpha."""
+    U = 0.37
+    ns = (64, 128, 256, 512)
+    sig, drift = zip(*(rates(name, U, n) for n in ns))
+    a = ALPHA[name]
+    scaled = [s * n ** (a - 1) for s, n in zip(sig, ns)]
+    assert max(scaled) / min(scaled) < 1.02, scaled
+    slope = np.polyfit(np.log(ns), np.log(sig), 1)[0]
+    assert slope == pytest.approx(1 - a, abs=0.03)
+    s512, w512 = table1_rates(name, U, 512)
+    assert sig[-1] / s512 == pytest.approx(1.0, abs=3e-3)
+    if name in ("FEC", "BEC"):
+        assert drift[-1] / w512 == pytest.approx(1.0, abs=3e-3)
+    if name == "CEC":           # no third-derivative (dispersive) term in Table 1
+        assert abs(drift[-1]) < 1e-2 * sig[-1]
