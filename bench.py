@@ -396,6 +396,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         extras["rotation_c1"] = rotation_measurement(torch, sl, stream)
         extras["resolution_f1"] = resolution_measurement(torch, sl, stream)
+        extras["shear_f3"] = shear_measurement(torch, sl, stream)
         extras["learned_c4"] = learned_measurement(torch, sl, stream)
 
     cpu = None
@@ -670,6 +671,47 @@ def resolution_measurement(torch, sl, stream, U=0.37, sizes=(64, 128, 256, 512))
             rec["drift_coeff_over_table1"] = drift[-1] / (k ** 3 * dx ** 2) / TABLE1_DRIFT[name](U)
         else:
             rec["drift_over_decay"] = drift[-1] / sig[-1]
+        out[name] = rec
+    return out
+
+
+def shear_measurement(torch, sl, stream, sizes=(128, 256, 512)):
+    """The 2D patch test of Sec. 5 (compact divergence-free shear, CFL 0.5, to
+    t = 64, FP64), every scheme, against the initial field carried along exact
+    trajectories: L1 error of the discontinuous square patch, relative L2 error
+    of a smooth Gaussian in its place and the orders between sizes, and the
+    time per step at the largest size."""
+    from paper_1606_06117_gb300 import workloads as W
+    out = {"sizes": list(sizes), "T": W.SHEAR_T, "cfl": 0.5, "dtype": "f64"}
+    exact = {}
+    for n in sizes:
+        for kind, f in (("patch", W.patch_indicator()), ("bump", W.bump())):
+            exact[(n, kind)] = W.shear_exact((n, n), f, device="cuda")
+    for name in ("CIR", "FEC", "BEC", "CEC"):
+        code = getattr(sl, name)
+        rec = {"patch_l1": [], "bump_rel_l2": []}
+        for n in sizes:
+            vel = W.shear_patch_velocity((n, n), device="cuda")
+            dt, nsteps = W.dt_for_cfl(W.SHEAR_T, vel.abs().max().item() * n, 0.5)
+            for kind, f in (("patch", W.patch_indicator()), ("bump", W.bump())):
+                x = W.on_grid((n, n), f, device="cuda")
+                y = torch.empty_like(x)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for k in range(nsteps):
+                    sl.sl_advect(y, x, vel, 2, [n, n, 1], [1.0 / n, 1.0 / n, 1.0], dt, code, sl.F64, k & 1, stream)
+                    x, y = y, x
+                torch.cuda.synchronize()
+                el = time.perf_counter() - t0
+                ex = exact[(n, kind)]
+                if kind == "patch":
+                    rec["patch_l1"].append((x - ex).abs().mean().item())
+                else:
+                    rec["bump_rel_l2"].append((torch.linalg.vector_norm(x - ex) / torch.linalg.vector_norm(ex)).item())
+            rec["steps"] = nsteps
+            rec["us_per_step"] = el / nsteps * 1e6
+        e = rec["bump_rel_l2"]
+        rec["bump_orders"] = [math.log2(e[i] / e[i + 1]) for i in range(len(e) - 1)]
         out[name] = rec
     return out
 

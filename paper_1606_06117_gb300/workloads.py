@@ -1,7 +1,9 @@
 """Seeded synthetic inputs shaped like the paper's workloads.
 
 This module only draws and evaluates input fields (initial scalars and
-velocities); it holds none of the advection arithmetic.  It serves both the
+velocities) and the exact solutions of the analytic workloads (the initial
+field carried along exact trajectories); it holds none of the advection
+schemes' arithmetic.  It serves both the
 CUDA path and the FP64 oracle, so that both see the same input values.
 
 All generators evaluate on cell centres x_i = (i + 1/2) * L / N of a periodic
@@ -146,23 +148,95 @@ def deformation_velocity(shape, device="cpu", dtype=torch.float64):
     return torch.stack([u.expand(shape), v.expand(shape), w.expand(shape)]).contiguous().to(dtype)
 
 
+# Final time of the patch test (Sec. 5 gives none): the largest speed is
+# 3.85e-3, so the patch moves by up to a quarter of the box.
+SHEAR_T = 64.0
+
+
+def shear_profile(s):
+    """Velocity profile of the 2D patch test (Sec. 5):
+    s (1 - s) (1/2 - s) (cos(2 pi s (1 - s)) + 1) / (2 pi^2)."""
+    return s * (1 - s) * (0.5 - s) * (torch.cos(TWO_PI * s * (1 - s)) + 1) / (2 * math.pi ** 2)
+
+
 def shear_patch_velocity(shape, device="cpu", dtype=torch.float64):
-    """The compact divergence-free shear of the paper's 2D patch test (Sec. 5) on the unit square."""
+    """The compact divergence-free shear of the paper's 2D patch test (Sec. 5) on
+    the unit square: u = profile(y), v = -profile(x)."""
     x, y = _mesh(shape, 1.0, device)
-
-    def prof(s):
-        return s * (1 - s) * (0.5 - s) * (torch.cos(TWO_PI * s * (1 - s)) + 1) / (2 * math.pi ** 2)
-
-    u = prof(y) + 0 * x
-    v = -prof(x) + 0 * y
+    u = shear_profile(y) + 0 * x
+    v = -shear_profile(x) + 0 * y
     return torch.stack([u.expand(shape), v.expand(shape)]).contiguous().to(dtype)
+
+
+def shear_stream(x, y):
+    """Stream function of the patch-test velocity, psi = P(x) + P(y) with
+    u = d psi / dy and v = -d psi / dx.  P' = profile integrates in
+    w = s (1 - s): P = (w sin(2 pi w) / (2 pi) + cos(2 pi w) / (4 pi^2) + w^2 / 2) / (4 pi^2)."""
+    def P(s):
+        w = s * (1 - s)
+        return (w * torch.sin(TWO_PI * w) / TWO_PI + torch.cos(TWO_PI * w) / (4 * math.pi ** 2) + w * w / 2) / (
+            4 * math.pi ** 2)
+    return P(x) + P(y)
+
+
+def shear_departure(x, y, T=SHEAR_T, nsub=512):
+    """Exact departure points: where the points (x, y) at time T were at time 0
+    under the patch-test velocity, by classical fourth-order Runge-Kutta
+    integration backwards in time with nsub steps (FP64), in the periodic box:
+    the profile is evaluated at coordinates reduced to [0, 1), and the points
+    are returned reduced.  The trajectories are level curves of shear_stream
+    (of the periodic box: curves below the saddle value circle the corners)."""
+    h = -T / nsub
+    x = x.to(torch.float64)
+    y = y.to(torch.float64)
+
+    def f(px, py):
+        return shear_profile(torch.remainder(py, 1.0)), -shear_profile(torch.remainder(px, 1.0))
+    for _ in range(nsub):
+        a1, b1 = f(x, y)
+        a2, b2 = f(x + 0.5 * h * a1, y + 0.5 * h * b1)
+        a3, b3 = f(x + 0.5 * h * a2, y + 0.5 * h * b2)
+        a4, b4 = f(x + h * a3, y + h * b3)
+        x = x + h / 6 * (a1 + 2 * a2 + 2 * a3 + a4)
+        y = y + h / 6 * (b1 + 2 * b2 + 2 * b3 + b4)
+    return torch.remainder(x, 1.0), torch.remainder(y, 1.0)
+
+
+def shear_exact(shape, initial, T=SHEAR_T, nsub=512, device="cpu", dtype=torch.float64):
+    """Exact solution of the patch test at time T on the cell centres: the
+    initial field initial(x0, y0) (a function of FP64 coordinate tensors) at the
+    exact departure points."""
+    x, y = _mesh(shape, 1.0, device)
+    x, y = torch.broadcast_tensors(x, y)
+    x0, y0 = shear_departure(x, y, T, nsub)
+    return initial(x0, y0).to(dtype)
+
+
+def patch_indicator(lo=0.25, hi=0.5):
+    """The square patch of Sec. 5 as a function of coordinates: 1 inside [lo, hi)^2."""
+    def f(x, y):
+        return ((x >= lo) & (x < hi) & (y >= lo) & (y < hi)).to(torch.float64)
+    return f
+
+
+def bump(center=(0.375, 0.375), sigma=0.06):
+    """A smooth Gaussian in the patch's place, exp(-|x - c|^2 / (2 sigma^2)), for
+    convergence orders under the same flow (below 4e-9 at the box edges)."""
+    def f(x, y):
+        return torch.exp(-((x - center[0]) ** 2 + (y - center[1]) ** 2) / (2 * sigma * sigma))
+    return f
 
 
 def square_patch(shape, lo=0.25, hi=0.5, device="cpu", dtype=torch.float64):
     """1 inside the square [lo, hi)^2, 0 outside (Sec. 5 patch test)."""
     x, y = _mesh(shape, 1.0, device)
-    inside = (x >= lo) & (x < hi) & (y >= lo) & (y < hi)
-    return inside.to(dtype)
+    return patch_indicator(lo, hi)(*torch.broadcast_tensors(x, y)).to(dtype)
+
+
+def on_grid(shape, f, device="cpu", dtype=torch.float64):
+    """A function of FP64 coordinate tensors (x, y) evaluated on the 2D cell centres."""
+    x, y = _mesh(shape, 1.0, device)
+    return f(*torch.broadcast_tensors(x, y)).to(dtype)
 
 
 def profile_1d(n, kind, device="cpu", dtype=torch.float64):

@@ -119,3 +119,74 @@ def test_random_modes_are_seeded_and_periodic():
     ref = sum(am * math.cos(float(k @ x) + p) for k, am, p in zip(m.k, m.amp, m.phase))
     assert a[7, 5, 2] == pytest.approx(ref, abs=1e-12)
     assert torch.is_tensor(W.abc_velocity((4, 4, 4)))
+
+
+# ------------------------------------------------------- Sec. 5 patch test (E5)
+def shear_case(n):
+    """Grid Courant numbers and step count of the patch test at n^2, CFL 0.5,
+    final time W.SHEAR_T (reached exactly)."""
+    shape = (n, n)
+    vel = W.shear_patch_velocity(shape).numpy()
+    dt, nsteps = W.dt_for_cfl(W.SHEAR_T, np.abs(vel).max() * n, 0.5)
+    return vel * (dt * n), nsteps
+
+
+def shear_errors(n, initial):
+    """(L1, relative L2) of each scheme's oracle solution against the initial
+    field carried along exact trajectories."""
+    shape = (n, n)
+    c, nsteps = shear_case(n)
+    phi0 = W.on_grid(shape, initial).numpy()
+    exact = W.shear_exact(shape, initial).numpy()
+    out = {}
+    for s in (O.CIR, O.FEC, O.BEC, O.CEC):
+        phi = O.run(phi0, c, s, nsteps)
+        out[s] = (np.abs(phi - exact).mean(), O.norms(phi, exact)[2])
+    return out
+
+
+def test_shear_reference_trajectories():
+    """The exact-trajectory reference of the patch test: the departure points
+    keep the closed-form stream function psi = P(x) + P(y) of the flow, whose
+    derivatives are the velocity of Sec. 5 (u = d psi / dy, v = -d psi / dx);
+    integrating forward again returns to the start; halving the Runge-Kutta
+    step changes nothing at 1e-9."""
+    x, y = torch.meshgrid(torch.linspace(0.01, 0.99, 41, dtype=torch.float64),
+                          torch.linspace(0.02, 0.98, 37, dtype=torch.float64), indexing="xy")
+    h = 1e-6
+    dpsi_dy = (W.shear_stream(x, y + h) - W.shear_stream(x, y - h)) / (2 * h)
+    dpsi_dx = (W.shear_stream(x + h, y) - W.shear_stream(x - h, y)) / (2 * h)
+    assert torch.allclose(dpsi_dy, W.shear_profile(y), atol=1e-9, rtol=0)
+    assert torch.allclose(-dpsi_dx, -W.shear_profile(x), atol=1e-9, rtol=0)
+    x0, y0 = W.shear_departure(x, y)
+    assert (W.shear_stream(x0, y0) - W.shear_stream(x, y)).abs().max() < 1e-11
+    x1, y1 = W.shear_departure(x0, y0, T=-W.SHEAR_T)
+
+    def pdist(a, b):
+        d = (a - b).abs()
+        return torch.minimum(d, 1 - d).max()
+    assert pdist(x1, x) < 1e-9 and pdist(y1, y) < 1e-9
+    x2, y2 = W.shear_departure(x, y, nsub=1024)
+    assert pdist(x2, x0) < 1e-9 and pdist(y2, y0) < 1e-9
+    assert pdist(x0, x) > 0.1            # the flow does move the points
+
+
+def test_shear_patch_ranking():
+    """Sec. 5 (figs. dis1, dis2): on the discontinuous square patch CIR has the
+    largest error and CEC the smallest; the four schemes rank
+    CEC < BEC < FEC < CIR at two resolutions."""
+    for n in (64, 128):
+        e = {s: v[0] for s, v in shear_errors(n, W.patch_indicator()).items()}
+        assert e[O.CEC] < e[O.BEC] < e[O.FEC] < e[O.CIR], (n, e)
+
+
+def test_shear_smooth_field_orders():
+    """Sec. 5: for regularly varying velocities the orders are those of constant
+    velocity, 1 / 2 / 2 / 3: a Gaussian in the patch's place, same flow, exact
+    trajectories, 64^2 -> 128^2."""
+    lo = {O.CIR: 0.7, O.FEC: 1.8, O.BEC: 1.8, O.CEC: 2.6}
+    hi = {O.CIR: 1.3, O.FEC: 2.3, O.BEC: 2.3, O.CEC: 3.4}
+    e64, e128 = shear_errors(64, W.bump()), shear_errors(128, W.bump())
+    for s in lo:
+        order = math.log2(e64[s][1] / e128[s][1])
+        assert lo[s] < order < hi[s], (s, order)
