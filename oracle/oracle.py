@@ -20,6 +20,9 @@ import threading
 import numpy as np
 
 CIR, FEC, BEC, CEC, CEC_DEF = 0, 1, 2, 3, 4
+# large Courant numbers (Sec. 4, eq. intro:CECcoefSL), split CEC in two readings:
+# correction at the departure cell (adopted) and the literal operator definitions
+CEC_SL, CEC_SL_LIT = 5, 6
 SCHEMES = {"CIR": CIR, "FEC": FEC, "BEC": BEC, "CEC": CEC}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -121,7 +124,7 @@ def scheme_on(phi, courant, scheme, axis=-1):
 
 
 def step(phi, courant, scheme, parity=0):
-    """One time step: CIR/FEC/BEC unsplit, CEC split with alternating sweep order."""
+    """One time step: CIR/FEC/BEC unsplit; CEC, CEC_SL, CEC_SL_LIT split with alternating sweep order."""
     phi, courant, n, ndim = _prep(phi, courant)
     out = np.empty_like(phi)
     _check(_load().orc_step(_ptr(out), _ptr(phi), _ptr(courant), _ptr(n, ctypes.c_int64),

@@ -24,7 +24,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { ORC_CIR = 0, ORC_FEC = 1, ORC_BEC = 2, ORC_CEC = 3, ORC_CEC_DEF = 4 };
+enum { ORC_CIR = 0, ORC_FEC = 1, ORC_BEC = 2, ORC_CEC = 3, ORC_CEC_DEF = 4, ORC_CEC_SL = 5, ORC_CEC_SL_LIT = 6 };
 
 static int64_t wrap(int64_t i, int64_t n)
 {
@@ -146,6 +146,23 @@ static int interp(double *out, const double *phi, const double *c,
  * so CEC_i = FEC_i + b_i (BEC_i - FEC_i) = FEC_i + (1 + U_i)/6 (delta_{i-s_i}
  * - delta_i), s_i = sgn C(i).  At U_i = 0, FEC_i = BEC_i and the combination
  * equals that common value for any a + b = 1 (s_i = 0 gives exactly that).
+ *
+ * Large Courant numbers (Sec. 4, eq. intro:CECcoefSL).  L_U above is already
+ * non-local: its corners bracket the departure point however far it is.  The
+ * CEC weights then come from the fractional part of U: 3a = 2 - 1/(U % 1),
+ * b = 1 - a.  Where the correction terms are taken is not stated; two readings
+ * (1D sweeps only, like ORC_CEC):
+ *   ORC_CEC_SL_LIT  the operator definitions unchanged, a FEC + b BEC with
+ *                   FEC = L_U[Phi] + delta/2 and BEC = L_U[Phi + delta/2],
+ *                   delta at the arrival cell.  Where U % 1 = 0 it takes FEC
+ *                   (L_U is then an exact shift, delta = 0 and FEC = BEC).
+ *   ORC_CEC_SL      the local scheme's correction taken at the departure cell:
+ *                   with m = trunc(C) and r = C - m, j = i - m, s = sgn r,
+ *                   CEC_i = L_U[Phi]_i + delta_j/2 + (1 + |r|)/6 (delta_{j-s} - delta_j).
+ *                   For constant velocity this is the local CEC at Courant
+ *                   number r shifted by m cells, so the scheme stays third
+ *                   order (the literal reading falls to second order); for
+ *                   |C| < 1 (m = 0) it is ORC_CEC term for term.
  */
 int orc_scheme_on(double *out, const double *phi, const double *c,
                   const int64_t n[3], int ndim, int axis, int scheme)
@@ -153,8 +170,8 @@ int orc_scheme_on(double *out, const double *phi, const double *c,
     const int64_t N = ncells(n);
     if (!out || !phi || !c || out == phi) return -1;
     if (scheme == ORC_CIR) return interp(out, phi, c, n, ndim, axis, +1);
-    if ((scheme == ORC_CEC || scheme == ORC_CEC_DEF) && axis < 0) return -1;
-    if (scheme < 0 || scheme > ORC_CEC_DEF) return -1;
+    if (scheme >= ORC_CEC && axis < 0) return -1;
+    if (scheme < 0 || scheme > ORC_CEC_SL_LIT) return -1;
 
     double *lphi = malloc(sizeof(double) * N);   /* L_U[Phi]           */
     double *bar = malloc(sizeof(double) * N);    /* Phi_bar            */
@@ -183,6 +200,37 @@ int orc_scheme_on(double *out, const double *phi, const double *c,
             const double b = 1.0 - a;
             out[i] = a * fec + b * tmp2[i];
         }
+    } else if (scheme == ORC_CEC_SL_LIT) {
+        const double *ca = c + (int64_t)axis * N;
+        for (int64_t i = 0; i < N; ++i) tmp[i] = phi[i] + (phi[i] - bar[i]) / 2.0;
+        interp(tmp2, tmp, c, n, ndim, axis, +1);              /* BEC */
+        for (int64_t i = 0; i < N; ++i) {
+            const double fec = lphi[i] + (phi[i] - bar[i]) / 2.0;
+            const double f = fmod(fabs(ca[i]), 1.0);
+            if (f == 0.0) {
+                out[i] = fec;
+            } else {
+                const double a = (2.0 - 1.0 / f) / 3.0;
+                out[i] = a * fec + (1.0 - a) * tmp2[i];
+            }
+        }
+    } else if (scheme == ORC_CEC_SL) {
+        const double *ca = c + (int64_t)axis * N;
+        for (int64_t i = 0; i < N; ++i) tmp[i] = phi[i] - bar[i];   /* delta */
+        for (int64_t z = 0; z < n[2]; ++z)
+            for (int64_t y = 0; y < n[1]; ++y)
+                for (int64_t x = 0; x < n[0]; ++x) {
+                    const int64_t i = (z * n[1] + y) * n[0] + x;
+                    const double C = ca[i];
+                    const double m = trunc(C), r = C - m;
+                    const int s = (r > 0.0) - (r < 0.0);
+                    int64_t qj[3] = {x, y, z}, qu[3] = {x, y, z};
+                    qj[axis] -= (int64_t)m;
+                    qu[axis] -= (int64_t)m + s;
+                    const double dj = tmp[at(n, qj[0], qj[1], qj[2])];
+                    const double du = tmp[at(n, qu[0], qu[1], qu[2])];
+                    out[i] = lphi[i] + dj / 2.0 + (1.0 + fabs(r)) / 6.0 * (du - dj);
+                }
     } else { /* ORC_CEC */
         const double *ca = c + (int64_t)axis * N;
         for (int64_t i = 0; i < N; ++i) tmp[i] = phi[i] - bar[i];   /* delta */
@@ -220,7 +268,8 @@ int orc_step(double *out, const double *phi, const double *c,
 {
     const int64_t N = ncells(n);
     if (!out || !phi || !c || out == phi || ndim < 1 || ndim > 3) return -1;
-    if (scheme != ORC_CEC) return orc_scheme_on(out, phi, c, n, ndim, -1, scheme);
+    if (scheme != ORC_CEC && scheme != ORC_CEC_SL && scheme != ORC_CEC_SL_LIT)
+        return orc_scheme_on(out, phi, c, n, ndim, -1, scheme);
 
     double *a = malloc(sizeof(double) * N);
     double *b = malloc(sizeof(double) * N);
@@ -228,7 +277,7 @@ int orc_step(double *out, const double *phi, const double *c,
     memcpy(a, phi, sizeof(double) * N);
     for (int k = 0; k < ndim; ++k) {
         const int axis = (parity & 1) ? ndim - 1 - k : k;
-        orc_scheme_on(b, a, c, n, ndim, axis, ORC_CEC);
+        orc_scheme_on(b, a, c, n, ndim, axis, scheme);
         double *t = a; a = b; b = t;
     }
     memcpy(out, a, sizeof(double) * N);
@@ -243,7 +292,8 @@ int orc_step(double *out, const double *phi, const double *c,
  * result at a cell equals the result, at the centre, of the same step on the
  * 7^ndim window around it treated as a periodic grid: the wrap-around inside
  * the window only changes intermediate values that the centre never reads.
- * cells holds ns (x, y, z) triples.
+ * cells holds ns (x, y, z) triples.  Returns -3, computing nothing, if any
+ * |C| > 1 (the window would be too narrow).
  */
 int orc_sample(double *out, const double *phi, const double *c,
                const int64_t n[3], int ndim, int scheme, int parity,
@@ -252,6 +302,8 @@ int orc_sample(double *out, const double *phi, const double *c,
     enum { R = 3, W = 2 * R + 1 };
     if (!out || !phi || !c || !cells || ndim < 1 || ndim > 3) return -1;
     const int64_t N = ncells(n);
+    for (int64_t i = 0; i < N * ndim; ++i)
+        if (fabs(c[i]) > 1.0) return -3;
     int64_t wn[3] = {1, 1, 1};
     for (int d = 0; d < ndim; ++d) wn[d] = W;
     const int64_t WN = wn[0] * wn[1] * wn[2];
