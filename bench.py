@@ -397,6 +397,8 @@ def run_ours(args):
         extras["rotation_c1"] = rotation_measurement(torch, sl, stream)
         extras["resolution_f1"] = resolution_measurement(torch, sl, stream)
         extras["shear_f3"] = shear_measurement(torch, sl, stream)
+        torch.cuda.empty_cache()
+        extras["large_cfl_f2"] = large_cfl_measurement(torch, sl, stream)
         extras["learned_c4"] = learned_measurement(torch, sl, stream)
 
     cpu = None
@@ -714,6 +716,62 @@ def shear_measurement(torch, sl, stream, sizes=(128, 256, 512)):
         rec["bump_orders"] = [math.log2(e[i] / e[i + 1]) for i in range(len(e) - 1)]
         out[name] = rec
     return out
+
+
+# Algorithmic bytes per cell of one FP32 wide CEC step: per axis sweep, L_U
+# (read Phi, u_d; write L) 12 B, L_{-U} with delta (read L, u_d, Phi; write
+# delta) 16 B, the departure-cell correction (read L, delta, u_d; write) 16 B.
+WIDE_CEC_BYTES_PER_CELL = 3 * (12 + 16 + 16)
+
+
+def large_cfl_measurement(torch, sl, stream, n=256, cfl=3.75, timed=20):
+    """Steps at a large Courant number (Sec. 4, eq. intro:CECcoefSL): the 256^3
+    ABC / 32-mode workload advanced by the non-local CEC step (sl_advect_wide)
+    at CFL 3.75 over the physical time of 100 local CEC steps at CFL 0.8.
+    Reports the time per step, the rate and its HBM roofline (132 B per cell,
+    unfused), and the round trip (forward, then back with -dt) against the
+    local step's 100 + 100 steps: relative L2 error and wall time for the same
+    physical time."""
+    phi, vel, sp, dt0 = workload(n, "cuda", torch)
+    dims = [n, n, n]
+    T = 100 * dt0
+    nsteps = int(math.ceil(T * 2.0 / sp[0] / cfl - 1e-12))     # max |u_d| = 2
+    dt = T / nsteps
+    need = sl.sl_advect_wide_workspace(3, dims, sl.CEC, sl.F32)
+    ws_t = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+    ws = ws_t.data_ptr() + (-ws_t.data_ptr()) % 256
+    a, b = phi.clone(), torch.empty_like(phi)
+
+    def fn(k):
+        sl.sl_advect_wide(b, a, vel, 3, dims, sp, dt, sl.CEC, sl.F32, k & 1, ws, need, stream)
+    fn(0)
+    fn(1)
+    ms = time_steps(torch, stream, fn, timed)
+    peak, kind = measured_hbm_peak()
+    gbs = WIDE_CEC_BYTES_PER_CELL * n ** 3 / (ms * 1e-3) / 1e9
+
+    def round_trip(step, count, h):
+        x, y = phi.clone(), torch.empty_like(phi)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(2 * count):
+            step(y, x, h if k < count else -h, k)
+            x, y = y, x
+        torch.cuda.synchronize()
+        return sl.sl_norms(x, phi, phi.numel(), sl.F32, stream)[2], time.perf_counter() - t0
+
+    wide_err, wide_s = round_trip(
+        lambda y, x, h, k: sl.sl_advect_wide(y, x, vel, 3, dims, sp, h, sl.CEC, sl.F32, k & 1, ws, need, stream),
+        nsteps, dt)
+    local_err, local_s = round_trip(
+        lambda y, x, h, k: sl.sl_advect(y, x, vel, 3, dims, sp, h, sl.CEC, sl.F32, k & 1, stream), 100, dt0)
+    sl.sl_device_status(stream)
+    return {"grid": dims, "cfl": dt * 2.0 / sp[0], "steps_for_T": nsteps, "ms_per_step": ms,
+            "gcell_s": n ** 3 / (ms * 1e-3) / 1e9,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_kind": kind, "bytes_per_cell": WIDE_CEC_BYTES_PER_CELL},
+            "roundtrip_rel_l2": wide_err, "roundtrip_seconds": wide_s,
+            "local_cfl_0.8": {"steps_for_T": 100, "roundtrip_rel_l2": local_err, "roundtrip_seconds": local_s}}
 
 
 def cec512_measurement(torch, sl, stream, n=512, timed=40):

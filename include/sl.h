@@ -226,6 +226,43 @@ int sl_batch_step(sl_batch *b, int step_index, void *stream);
 int sl_batch_destroy(sl_batch *b);
 
 /*
+ * One time step at any Courant number (Sec. 4: semi-Lagrangian schemes may
+ * exceed CFL 1 when the interpolation uses non-neighbouring points).  The
+ * interpolation is non-local: its corners bracket the departure point
+ * X = i - C (cell units) however far it is, so an integer C is an exact shift.
+ *   SL_CIR, SL_FEC, SL_BEC  the operator compositions of Sec. 2 (eqs.
+ *                  intro:FEC, intro:BEC) with the unsplit multilinear
+ *                  interpolation (eq. CIR2D and its 3D tensor product).
+ *   SL_CEC         split 1D sweeps (order as sl_advect) with the weights of
+ *                  eq. intro:CECcoefSL, 3a = 2 - 1/(U % 1), b = 1 - a, and the
+ *                  correction of the local scheme taken at the departure cell:
+ *                  m = trunc(C), r = C - m, j = i - m, s = sgn r,
+ *                  CEC_i = L_U[Phi]_i + delta_j/2 + (1 + |r|)/6 (delta_{j-s} - delta_j).
+ *                  For constant velocity this is the upwind cubic Lagrange
+ *                  interpolation at the departure point (third order at every
+ *                  CFL); for |C| < 1 it equals sl_advect's SL_CEC up to rounding.
+ * Same arguments as sl_advect, with dtype SL_F32 or SL_F64 (SL_F32_D64 returns
+ * SL_ERR_UNSUPPORTED), and dims[1], dims[2] <= 65535 (else SL_ERR_UNSUPPORTED).
+ *   workspace        device memory of at least sl_advect_wide_workspace()
+ *                    bytes, 256-byte aligned, owned by the caller; it holds
+ *                    intermediate fields and is overwritten.  May be NULL when
+ *                    that size is 0 (SL_CIR).
+ *   workspace_bytes  its size.
+ * The call allocates nothing and only enqueues kernels on stream (one per
+ * interpolation call: 1 / 2 / 3 for CIR / FEC / BEC, 3 per axis for CEC).  A
+ * non-finite or huge departure point sets SL_DEV_CFL and is replaced by the
+ * arrival cell.
+ * Errors: those of sl_advect; SL_ERR_ARG for a workspace that is too small or
+ * misaligned; SL_ERR_ALIAS when out, in, vel and workspace overlap (out and
+ * workspace must each be disjoint from every other buffer).
+ */
+int64_t sl_advect_wide_workspace(int ndim, const int64_t dims[3], int scheme, int dtype);
+int sl_advect_wide(void *out, const void *in, const void *vel, int ndim,
+                   const int64_t dims[3], const double spacing[3], double dt,
+                   int scheme, int dtype, int step_parity, void *workspace,
+                   int64_t workspace_bytes, void *stream);
+
+/*
  * Autotune: time the candidate launch shapes of the fused SL_CEC kernel for
  * this grid on the given stream (device buffers supplied by the caller; the
  * step is run several times, so out is overwritten) and cache the fastest for

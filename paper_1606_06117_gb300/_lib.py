@@ -32,7 +32,8 @@ EXPORTS = ("sl_version", "sl_last_error", "sl_init", "sl_advect", "sl_advect_mul
            "sl_batch_step", "sl_batch_destroy", "sl_autotune", "sl_norms_static",
            "sl_corrector_param_count", "sl_corrector_create", "sl_corrector_destroy", "sl_corrector_get_params",
            "sl_corrector_set_params", "sl_corrector_add_samples", "sl_corrector_get_rows", "sl_corrector_train",
-           "sl_corrector_reset", "sl_advect_learned", "sl_selftest_wait_timeout")
+           "sl_corrector_reset", "sl_advect_learned", "sl_selftest_wait_timeout", "sl_advect_wide_workspace",
+           "sl_advect_wide")
 
 
 class SLError(RuntimeError):
@@ -94,6 +95,8 @@ def load(path: str | None = None):
             "sl_corrector_reset": ([vp], i),
             "sl_advect_learned": ([vp, vp, vp, vp, i, i64p, dp, d, i, i, d, ctypes.POINTER(i), dp, vp], i),
             "sl_selftest_wait_timeout": ([ctypes.c_uint, vp], i),
+            "sl_advect_wide_workspace": ([i, i64p, i, i], ctypes.c_int64),
+            "sl_advect_wide": ([vp, vp, vp, i, i64p, dp, d, i, i, i, vp, ctypes.c_int64, vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -170,6 +173,20 @@ def sl_advect_multi(outs, ins, vel, ndim, dims, spacing, dt, scheme, dtype, step
 def sl_advect_host(out, inp, vel, ndim, dims, spacing, dt, scheme, dtype, step_parity=0, stream=None):
     return _check(load().sl_advect_host(_ptr(out), _ptr(inp), _ptr(vel), ndim, _i64(dims), _f64(spacing), float(dt),
                                         int(scheme), int(dtype), int(step_parity), _stream(stream)))
+
+
+def sl_advect_wide_workspace(ndim, dims, scheme, dtype):
+    n = load().sl_advect_wide_workspace(int(ndim), _i64(dims), int(scheme), int(dtype))
+    if n < 0:
+        raise SLError(int(n), load().sl_last_error().decode())
+    return n
+
+
+def sl_advect_wide(out, inp, vel, ndim, dims, spacing, dt, scheme, dtype, step_parity=0, workspace=None,
+                   workspace_bytes=0, stream=None):
+    return _check(load().sl_advect_wide(_ptr(out), _ptr(inp), _ptr(vel), ndim, _i64(dims), _f64(spacing), float(dt),
+                                        int(scheme), int(dtype), int(step_parity), _ptr(workspace),
+                                        int(workspace_bytes), _stream(stream)))
 
 
 def sl_release_host_staging():
@@ -326,4 +343,31 @@ def advect(phi: torch.Tensor, vel: torch.Tensor, dt: float, spacing=None, scheme
         out = torch.empty_like(phi)
     sc = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     sl_advect(out, phi, vel, ndim, dims, sp, dt, sc, dtype_code(phi.dtype, delta64), parity, stream)
+    return out
+
+
+def advect_wide(phi: torch.Tensor, vel: torch.Tensor, dt: float, spacing=None, scheme="CEC", parity: int = 0,
+                out: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """One step at any Courant number (sl_advect_wide) on CUDA tensors; allocates
+    ``out`` and the workspace (a uint8 CUDA tensor) when they are None."""
+    ndim, dims, sp = geometry(phi, spacing)
+    if not (phi.is_cuda and vel.is_cuda):
+        raise ValueError("advect_wide runs on CUDA tensors only")
+    if vel.shape != (ndim,) + tuple(phi.shape) or vel.dtype != phi.dtype:
+        raise ValueError("vel must be (ndim, *phi.shape) with phi's dtype")
+    phi = phi.contiguous()
+    vel = vel.contiguous()
+    if out is None:
+        out = torch.empty_like(phi)
+    sc = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    dc = dtype_code(phi.dtype)
+    need = sl_advect_wide_workspace(ndim, dims, sc, dc)
+    if workspace is None and need > 0:
+        workspace = torch.empty(need + 256, dtype=torch.uint8, device=phi.device)
+    ws, nbytes = None, 0
+    if workspace is not None:
+        base = workspace.data_ptr()
+        off = (-base) % 256
+        ws, nbytes = base + off, workspace.numel() * workspace.element_size() - off
+    sl_advect_wide(out, phi, vel, ndim, dims, sp, dt, sc, dc, parity, ws, nbytes, stream)
     return out

@@ -1,0 +1,288 @@
+// k_wide.cu -- steps at any Courant number, with non-local interpolation: the
+// corners of L_U bracket the departure point X = i - C (cell units) however far
+// it is, so |C| > 1 needs no wider stencil than |C| < 1, only a gather from
+// further away (Sec. 4: semi-Lagrangian schemes may exceed CFL 1 when the
+// interpolation uses non-neighbouring points).
+//
+//   CIR, FEC, BEC  the operator compositions of Sec. 2 (eqs. intro:FEC,
+//                  intro:BEC) with the unsplit multilinear L_U (eq. CIR2D and
+//                  its 3D tensor product).
+//   CEC            split 1D sweeps (Sec. 5 eqs. split:1-2, order x,y,z on even
+//                  steps and z,y,x on odd steps) with the weights of eq.
+//                  intro:CECcoefSL, 3a = 2 - 1/(U % 1), b = 1 - a, and the
+//                  correction of the local scheme taken at the departure cell:
+//                  with m = trunc(C), r = C - m, j = i - m, s = sgn r,
+//                  CEC_i = L_U[Phi]_i + delta_j/2 + (1 + |r|)/6 (delta_{j-s} - delta_j).
+//                  For constant velocity this is the local CEC at Courant
+//                  number r shifted by m cells (third order); for |C| < 1 it
+//                  is the local CEC.
+//
+// Unfused: one gather kernel per interpolation call, each with the scheme's
+// pointwise combination as its epilogue, and one gather kernel for the CEC
+// correction.  Intermediate fields live in a caller-owned workspace.
+#include "sl_internal.h"
+
+namespace sl {
+namespace {
+
+enum Epi { EPI_NONE = 0, EPI_FEC = 1, EPI_BEC_IN = 2, EPI_DELTA = 3 };
+
+constexpr int kWideBlock = 128;
+
+struct WideGeo {
+    int n[3];          // cells per axis (x, y, z)
+    int64_t ncell;     // n[0] n[1] n[2]
+    double s[3];       // dt / dx_d: Courant number = u_d s_d
+    unsigned *status;  // SL_DEV_CFL: a non-finite or huge departure point
+};
+
+// Integer part and fraction of a displacement D (cell units): D = fl + f,
+// f in [0, 1).  A non-finite displacement, or one whose integer part a cell
+// index cannot hold, is flagged and replaced by 0 so that every index stays
+// in bounds.
+template <typename T>
+__device__ __forceinline__ int64_t floor_split(T D, T &f, bool &bad)
+{
+    if (!(fabs(D) < T(1.0e15))) {
+        bad = true;
+        D = T(0);
+    }
+    const T fl = floor(D);
+    f = D - fl;
+    return (int64_t)fl;
+}
+
+// v reduced into [0, n).  Departure points within one period of the grid take
+// a compare and an add; the 64-bit remainder (slow) only runs beyond that.
+__device__ __forceinline__ int wrap64(int64_t v, int n)
+{
+    if (v >= 0 && v < n) return (int)v;
+    if (v < 0 && v >= -(int64_t)n) return (int)(v + n);
+    if (v >= n && v < 2 * (int64_t)n) return (int)(v - n);
+    int64_t r = v % n;
+    return (int)(r < 0 ? r + n : r);
+}
+
+__device__ __forceinline__ int64_t cell_at(const WideGeo &g, int x, int y, int z)
+{
+    return ((int64_t)z * g.n[1] + y) * g.n[0] + x;
+}
+
+// Each thread takes the cells (x, y0 + k, z), k < kWideRows: a warp's loads of
+// one k are coalesced along x, and the rows' loads are issued together (the
+// velocity of all rows, then all corners), so that several independent gathers
+// are in flight per thread.
+constexpr int kWideRows = 4;
+
+// out = epilogue(L_{dir U}[src]) at every cell.  AX < 0: the multilinear
+// operator on NDIM axes; AX >= 0: the 1D operator along that axis.  dir = +1
+// is L_U (departure i - C), dir = -1 is L_{-U} (departure i + C, -u at its own
+// arrival cell).
+template <typename T, int NDIM, int AX, int EPI>
+__global__ void __launch_bounds__(kWideBlock)
+k_wide_interp(T *__restrict__ out, const T *__restrict__ src, const T *__restrict__ vel, const T *__restrict__ aux0,
+              const T *__restrict__ aux1, WideGeo g, int dir)
+{
+    constexpr int R = kWideRows;
+    const int x = blockIdx.x * kWideBlock + threadIdx.x, y0 = blockIdx.y * R, z = blockIdx.z;
+    bool bad = false;
+    bool on[R];
+    int64_t cell[R];
+    T C[R][3];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        on[k] = x < g.n[0] && y0 + k < g.n[1];
+        cell[k] = on[k] ? cell_at(g, x, y0 + k, z) : 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const bool moves = AX < 0 ? d < NDIM : d == AX;
+            C[k][d] = moves && on[k] ? vel[(int64_t)d * g.ncell + cell[k]] * T(g.s[d]) : T(0);
+        }
+    }
+    T val[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int pos[3] = {x, y0 + k, z};
+        int b0[3] = {pos[0], pos[1], pos[2]}, b1[3] = {pos[0], pos[1], pos[2]};
+        T f[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const bool moves = AX < 0 ? d < NDIM : d == AX;
+            if (moves) {
+                const int64_t fl = floor_split<T>(T(-dir) * C[k][d], f[d], bad);
+                b0[d] = wrap64((int64_t)pos[d] + fl, g.n[d]);
+                b1[d] = b0[d] + 1 == g.n[d] ? 0 : b0[d] + 1;
+            }
+        }
+        val[k] = T(0);
+        if (!on[k]) continue;
+        if constexpr (AX >= 0) {
+            int q0[3] = {pos[0], pos[1], pos[2]}, q1[3] = {pos[0], pos[1], pos[2]};
+            q0[AX] = b0[AX];
+            q1[AX] = b1[AX];
+            const T a = src[cell_at(g, q0[0], q0[1], q0[2])], b = src[cell_at(g, q1[0], q1[1], q1[2])];
+            val[k] = a + f[AX] * (b - a);
+        } else {
+            // corners weighted by prod_d (1 - f_d | f_d), lerped along x, then y, then z,
+            // each lerp as a + f (b - a) so that a constant field stays exact
+            T c[2];
+#pragma unroll
+            for (int h = 0; h < (NDIM == 3 ? 2 : 1); ++h) {
+                const int zz = NDIM == 3 ? (h ? b1[2] : b0[2]) : z;
+                const T a00 = src[cell_at(g, b0[0], b0[1], zz)], a10 = src[cell_at(g, b1[0], b0[1], zz)];
+                const T a01 = src[cell_at(g, b0[0], b1[1], zz)], a11 = src[cell_at(g, b1[0], b1[1], zz)];
+                const T e0 = a00 + f[0] * (a10 - a00);
+                const T e1 = a01 + f[0] * (a11 - a01);
+                c[h] = e0 + f[1] * (e1 - e0);
+            }
+            val[k] = NDIM == 3 ? c[0] + f[2] * (c[1] - c[0]) : c[0];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        if (!on[k]) continue;
+        const int64_t i = cell[k];
+        const T v = val[k];
+        if constexpr (EPI == EPI_NONE) out[i] = v;
+        if constexpr (EPI == EPI_FEC) out[i] = aux1[i] + (aux0[i] - v) * T(0.5);
+        if constexpr (EPI == EPI_BEC_IN) out[i] = aux0[i] + (aux0[i] - v) * T(0.5);
+        if constexpr (EPI == EPI_DELTA) out[i] = aux0[i] - v;
+    }
+    flag_cfl(g.status, bad);
+}
+
+// The CEC sweep's output along AX from L_U[Phi] (lphi) and delta = Phi - Phi_bar:
+// CEC_i = lphi_i + delta_j/2 + (1 + |r|)/6 (delta_{j-s} - delta_j), m = trunc(C_i),
+// r = C_i - m, j = i - m, s = sgn r.
+template <typename T, int AX>
+__global__ void __launch_bounds__(kWideBlock)
+k_wide_cec(T *__restrict__ out, const T *__restrict__ lphi, const T *__restrict__ delta, const T *__restrict__ vel,
+           WideGeo g)
+{
+    constexpr int R = kWideRows;
+    const int x = blockIdx.x * kWideBlock + threadIdx.x, y0 = blockIdx.y * R, z = blockIdx.z;
+    bool bad = false;
+    bool on[R];
+    int64_t cell[R];
+    T C[R], L[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        on[k] = x < g.n[0] && y0 + k < g.n[1];
+        cell[k] = on[k] ? cell_at(g, x, y0 + k, z) : 0;
+        C[k] = on[k] ? vel[(int64_t)AX * g.ncell + cell[k]] * T(g.s[AX]) : T(0);
+        L[k] = on[k] ? lphi[cell[k]] : T(0);
+    }
+    T dj[R], du[R], r[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        T c = C[k];
+        if (!(fabs(c) < T(1.0e15))) {
+            bad = true;
+            c = T(0);
+        }
+        const T m = trunc(c);
+        r[k] = c - m;
+        const int s = (r[k] > T(0)) - (r[k] < T(0));
+        const int pos[3] = {x, y0 + k, z};
+        int qj[3] = {pos[0], pos[1], pos[2]}, qu[3] = {pos[0], pos[1], pos[2]};
+        qj[AX] = wrap64((int64_t)pos[AX] - (int64_t)m, g.n[AX]);
+        qu[AX] = wrap64((int64_t)pos[AX] - (int64_t)m - s, g.n[AX]);
+        dj[k] = on[k] ? delta[cell_at(g, qj[0], qj[1], qj[2])] : T(0);
+        du[k] = on[k] ? delta[cell_at(g, qu[0], qu[1], qu[2])] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+        if (on[k]) out[cell[k]] = L[k] + dj[k] * T(0.5) + (T(1) + fabs(r[k])) * T(1.0 / 6.0) * (du[k] - dj[k]);
+    flag_cfl(g.status, bad);
+}
+
+dim3 wide_grid(const WideGeo &g)
+{
+    return dim3((g.n[0] + kWideBlock - 1) / kWideBlock, (g.n[1] + kWideRows - 1) / kWideRows, g.n[2]);
+}
+
+template <typename T, int NDIM, int AX, int EPI>
+cudaError_t interp(T *out, const T *src, const T *vel, const T *aux0, const T *aux1, const WideGeo &g, int dir,
+                   cudaStream_t st)
+{
+    k_wide_interp<T, NDIM, AX, EPI><<<wide_grid(g), kWideBlock, 0, st>>>(out, src, vel, aux0, aux1, g, dir);
+    return cudaGetLastError();
+}
+
+template <typename T, int AX>
+cudaError_t sweep(T *dst, const T *src, const T *vel, T *w0, T *w1, const WideGeo &g, cudaStream_t st)
+{
+    cudaError_t e = interp<T, 3, AX, EPI_NONE>(w0, src, vel, nullptr, nullptr, g, +1, st);             // L_U[Phi]
+    if (e == cudaSuccess) e = interp<T, 3, AX, EPI_DELTA>(w1, w0, vel, src, nullptr, g, -1, st);       // delta
+    if (e != cudaSuccess) return e;
+    k_wide_cec<T, AX><<<wide_grid(g), kWideBlock, 0, st>>>(dst, w0, w1, vel, g);
+    return cudaGetLastError();
+}
+
+template <typename T, int NDIM>
+cudaError_t unsplit(int scheme, T *out, const T *in, const T *vel, T *w0, T *w1, const WideGeo &g, cudaStream_t st)
+{
+    if (scheme == 0) return interp<T, NDIM, -1, EPI_NONE>(out, in, vel, nullptr, nullptr, g, +1, st);
+    cudaError_t e = interp<T, NDIM, -1, EPI_NONE>(w0, in, vel, nullptr, nullptr, g, +1, st);           // L_U[Phi]
+    if (e != cudaSuccess) return e;
+    if (scheme == 1) return interp<T, NDIM, -1, EPI_FEC>(out, w0, vel, in, w0, g, -1, st);
+    e = interp<T, NDIM, -1, EPI_BEC_IN>(w1, w0, vel, in, nullptr, g, -1, st);                           // Phi + delta/2
+    if (e != cudaSuccess) return e;
+    return interp<T, NDIM, -1, EPI_NONE>(out, w1, vel, nullptr, nullptr, g, +1, st);
+}
+
+template <typename T>
+cudaError_t run(int scheme, const void *in_v, void *out_v, const void *vel_v, int ndim, const WideGeo &g, int parity,
+                void *work, cudaStream_t st)
+{
+    const T *in = static_cast<const T *>(in_v), *vel = static_cast<const T *>(vel_v);
+    T *out = static_cast<T *>(out_v);
+    const size_t fb = wide_field_bytes(g.ncell, sizeof(T));
+    T *w[4];
+    for (int k = 0; k < 4; ++k) w[k] = reinterpret_cast<T *>(static_cast<char *>(work) + k * fb);
+    if (scheme != 3) return ndim == 3 ? unsplit<T, 3>(scheme, out, in, vel, w[0], w[1], g, st)
+                                      : unsplit<T, 2>(scheme, out, in, vel, w[0], w[1], g, st);
+    // split CEC: in -> w2 (-> w3) -> out
+    const T *src = in;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < ndim && e == cudaSuccess; ++k) {
+        const int axis = (parity & 1) ? ndim - 1 - k : k;
+        T *dst = k == ndim - 1 ? out : w[2 + (k & 1)];
+        e = axis == 0 ? sweep<T, 0>(dst, src, vel, w[0], w[1], g, st)
+                      : (axis == 1 ? sweep<T, 1>(dst, src, vel, w[0], w[1], g, st)
+                                   : sweep<T, 2>(dst, src, vel, w[0], w[1], g, st));
+        src = dst;
+    }
+    return e;
+}
+
+}  // namespace
+
+size_t wide_field_bytes(int64_t ncell, size_t elem) { return ((size_t)ncell * elem + 255) & ~(size_t)255; }
+
+int wide_fields(int scheme, int ndim)
+{
+    switch (scheme) {
+    case 0: return 0;
+    case 1: return 1;
+    case 2: return 2;
+    default: return ndim == 3 ? 4 : 3;
+    }
+}
+
+cudaError_t launch_wide(int dtype, int scheme, const void *in, void *out, const void *vel, int ndim,
+                        const int64_t dims[3], const double s[3], int parity, void *work, unsigned *status,
+                        cudaStream_t st)
+{
+    WideGeo g;
+    for (int d = 0; d < 3; ++d) {
+        g.n[d] = (int)dims[d];
+        g.s[d] = d < ndim ? s[d] : 0.0;
+    }
+    g.ncell = dims[0] * dims[1] * dims[2];
+    g.status = status;
+    return dtype == 1 ? run<double>(scheme, in, out, vel, ndim, g, parity, work, st)
+                      : run<float>(scheme, in, out, vel, ndim, g, parity, work, st);
+}
+
+}  // namespace sl

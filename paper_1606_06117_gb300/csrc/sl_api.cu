@@ -571,6 +571,44 @@ int sl_batch_destroy(sl_batch *b)
     return SL_OK;
 }
 
+int64_t sl_advect_wide_workspace(int ndim, const int64_t dims[3], int scheme, int dtype)
+{
+    if (scheme < SL_CIR || scheme > SL_CEC) return fail(SL_ERR_ARG, "unknown scheme %d", scheme);
+    if (dtype != SL_F32 && dtype != SL_F64) return fail(SL_ERR_UNSUPPORTED, "wide steps take SL_F32 or SL_F64");
+    const double unit[3] = {1.0, 1.0, 1.0};
+    double s[3];
+    int rc = check_geometry(ndim, dims, unit, 1.0, dtype, s);
+    if (rc) return rc;
+    return (int64_t)wide_fields(scheme, ndim) * (int64_t)wide_field_bytes(ncell_of(dims), elem_size(dtype));
+}
+
+int sl_advect_wide(void *out, const void *in, const void *vel, int ndim, const int64_t dims[3],
+                   const double spacing[3], double dt, int scheme, int dtype, int step_parity, void *workspace,
+                   int64_t workspace_bytes, void *stream)
+{
+    if (!out || !in || !vel) return fail(SL_ERR_ARG, "out, in and vel must not be NULL");
+    const int64_t need = sl_advect_wide_workspace(ndim, dims, scheme, dtype);
+    if (need < 0) return (int)need;
+    double s[3];
+    int rc = check_geometry(ndim, dims, spacing, dt, dtype, s);
+    if (rc) return rc;
+    if (dims[1] > 65535 || dims[2] > 65535) return fail(SL_ERR_UNSUPPORTED, "wide steps need dims[1], dims[2] <= 65535");
+    if (workspace_bytes < need || (need > 0 && !workspace))
+        return fail(SL_ERR_ARG, "workspace of %lld bytes needed, %lld given", (long long)need, (long long)workspace_bytes);
+    if (need > 0 && (reinterpret_cast<uintptr_t>(workspace) & 255u)) return fail(SL_ERR_ARG, "workspace must be 256-byte aligned");
+    const size_t fb = (size_t)ncell_of(dims) * elem_size(dtype);
+    if (overlap(out, fb, in, fb) || overlap(out, fb, vel, fb * ndim)) return fail(SL_ERR_ALIAS, "out overlaps an input");
+    if (need > 0 && (overlap(workspace, (size_t)need, in, fb) || overlap(workspace, (size_t)need, vel, fb * ndim) ||
+                     overlap(workspace, (size_t)need, out, fb)))
+        return fail(SL_ERR_ALIAS, "workspace overlaps a field");
+    DevCtx *c = ctx_get();
+    if (!c) return fail(SL_ERR_CUDA, "could not create the device context");
+    const cudaError_t e = launch_wide(dtype, scheme, in, out, vel, ndim, dims, s, step_parity, workspace, c->status,
+                                      static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "wide step launch");
+    return SL_OK;
+}
+
 int sl_autotune(void *out, const void *in, const void *vel, int ndim, const int64_t dims[3], const double spacing[3],
                 double dt, int dtype, int *tile_z, void *stream)
 {

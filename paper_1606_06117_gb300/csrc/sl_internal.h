@@ -89,6 +89,16 @@ cudaError_t launch_cec_fast(const FastInst &one, const FastInst *dev_table, int 
                             unsigned *status, int grid_req, cudaStream_t st);
 int fast_grid(int parity);
 
+// Steps at any Courant number (k_wide.cu): non-local interpolation, unfused
+// kernels, intermediate fields in a caller-owned workspace of wide_fields()
+// fields of wide_field_bytes() each (256-byte aligned).  Grids launch as
+// (x blocks, ny, nz), so ny and nz must be at most 65535.
+size_t wide_field_bytes(int64_t ncell, size_t elem);
+int wide_fields(int scheme, int ndim);
+cudaError_t launch_wide(int dtype, int scheme, const void *in, void *out, const void *vel, int ndim,
+                        const int64_t dims[3], const double s[3], int parity, void *work, unsigned *status,
+                        cudaStream_t st);
+
 // Records a thread-local error message (read by sl_last_error) and returns code.
 int set_error(int code, const char *msg);
 

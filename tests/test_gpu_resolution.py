@@ -123,3 +123,35 @@ def test_resolution_study_matches_table1(name):
         assert drift[-1] / w512 == pytest.approx(1.0, abs=3e-3)
     if name == "CEC":           # no third-derivative (dispersive) term in Table 1
         assert abs(drift[-1]) < 1e-2 * sig[-1]
+
+
+def test_local_stencils_beyond_cfl_one():
+    """Sec. 3: the local kernels keep the neighbour stencil beyond U = 1 (an
+    extrapolation, flagged in the status word).  Their one-step amplification
+    is still the printed symbol: BEC's stays within 1 up to U = 1.5 and exceeds
+    it beyond; CIR, FEC and CEC exceed 1 at U = 1.2.  Over 400 steps of BEC the
+    L2 norm of a random field does not grow at U = 1.4 and grows by orders of
+    magnitude at U = 1.6."""
+    for U in (1.2, 1.4, 1.6):
+        for k in (3, 11, 21):
+            th = 2 * math.pi * k / 64
+            g, u = gpu_symbol("BEC", U, k, 0, 64, "f64")
+            assert abs(g - closed_form("BEC", u, th)) < 1e-13, (U, k)
+    peak = {U: max(abs(gpu_symbol("BEC", U, k, 0, 64, "f64")[0]) for k in range(1, 33)) for U in (1.2, 1.4, 1.6)}
+    assert peak[1.2] <= 1 + 1e-13 and peak[1.4] <= 1 + 1e-13 and peak[1.6] > 1.5, peak
+    for name in ("CIR", "FEC", "CEC"):
+        assert max(abs(gpu_symbol(name, 1.2, k, 0, 64, "f64")[0]) for k in range(1, 33)) > 1.1, name
+    rng = np.random.default_rng(7)
+    phi0 = torch.from_numpy(rng.standard_normal((8, 32, 64))).to(DEV)
+    growth = {}
+    for U in (1.4, 1.6):
+        vel = torch.zeros((3, 8, 32, 64), dtype=torch.float64, device=DEV)
+        vel[0] = U
+        phi = phi0.clone()
+        for s in range(400):
+            phi = sl.advect(phi, vel, 1.0, [1.0, 1.0, 1.0], "BEC", s)
+        growth[U] = (torch.linalg.vector_norm(phi) / torch.linalg.vector_norm(phi0)).item()
+    sl.sl_device_status()   # the runs flag |C| > 1
+    # constant velocity makes the step a circulant (normal) operator, so its L2
+    # norm cannot grow while every |g| <= 1
+    assert growth[1.4] <= 1 + 1e-9 and growth[1.6] > 1e3, growth
