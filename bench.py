@@ -718,18 +718,17 @@ def shear_measurement(torch, sl, stream, sizes=(128, 256, 512)):
     return out
 
 
-# Algorithmic bytes per cell of one FP32 wide CEC step: per axis sweep, L_U
-# (read Phi, u_d; write L) 12 B, L_{-U} with delta (read L, u_d, Phi; write
-# delta) 16 B, the departure-cell correction (read L, delta, u_d; write) 16 B.
-WIDE_CEC_BYTES_PER_CELL = 3 * (12 + 16 + 16)
+# Algorithmic bytes per cell of one FP32 wide CEC step whose lines fit the
+# fused sweep (k_wide_sweep): per axis, read Phi and u_d, write the result.
+WIDE_CEC_BYTES_PER_CELL = 3 * 12
 
 
 def large_cfl_measurement(torch, sl, stream, n=256, cfl=3.75, timed=20):
     """Steps at a large Courant number (Sec. 4, eq. intro:CECcoefSL): the 256^3
     ABC / 32-mode workload advanced by the non-local CEC step (sl_advect_wide)
     at CFL 3.75 over the physical time of 100 local CEC steps at CFL 0.8.
-    Reports the time per step, the rate and its HBM roofline (132 B per cell,
-    unfused), and the round trip (forward, then back with -dt) against the
+    Reports the time per step, the rate and its HBM roofline (36 B per cell:
+    three fused line sweeps), and the round trip (forward, then back with -dt) against the
     local step's 100 + 100 steps: relative L2 error and wall time for the same
     physical time."""
     phi, vel, sp, dt0 = workload(n, "cuda", torch)

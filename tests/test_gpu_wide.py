@@ -42,7 +42,9 @@ def oracle_of(phi, courant, scheme, parity):
     return O.step(phi.double().cpu().numpy(), courant, ORACLE[scheme], parity)
 
 
-SHAPES = [(12, 10, 16), (9, 20, 24), (5, 7, 33), (40, 56), (17, 3)]
+# the last two have lines along x too long for the fused shared-memory sweep
+# (FP64 beyond 4096 cells, FP32 beyond 8192), so their x sweep takes the three gathers
+SHAPES = [(12, 10, 16), (9, 20, 24), (5, 7, 33), (40, 56), (17, 3), (6, 4100), (3, 8200)]
 
 
 @pytest.mark.parametrize("cmax", [0.9, 2.5, 4.2])
