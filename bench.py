@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the per-scheme and batched side measurements")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed CEC steps (for ncu); prints the plain timing line")
+    ap.add_argument("--profile-wide", action="store_true",
+                    help="only run warmup + steps wide CEC steps (CFL 3.64) on the workload, for ncu")
     ap.add_argument("--profile-learned", action="store_true",
                     help="only warm-up and timed learned-corrector steps (untrained weights; for ncu)")
     ap.add_argument("--scheme", choices=["CIR", "FEC", "BEC", "CEC"], default="CEC",
@@ -303,6 +305,20 @@ def run_ours(args):
     dims = [n, n, n]
     a, b = phi.clone(), torch.empty_like(phi)
     stream = torch.cuda.current_stream()
+    if args.profile_wide:
+        # the large-CFL step of large_cfl_measurement: 22 steps cover 100 steps of CFL 0.8
+        dtw = 100 * dt / int(math.ceil(100 * dt * 2.0 / sp[0] / 3.75 - 1e-12))
+        need = sl.sl_advect_wide_workspace(3, dims, sl.CEC, sl.F32)
+        ws_t = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+        ws = ws_t.data_ptr() + (-ws_t.data_ptr()) % 256
+        for k in range(args.warmup + args.steps):
+            sl.sl_advect_wide(b, a, vel, 3, dims, sp, dtw, sl.CEC, sl.F32, k & 1, ws, need, stream)
+            a, b = b, a
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile_wide_run": True, "steps": args.steps}), flush=True)
+        return
+
     if args.profile_learned:
         # the learned step's work does not depend on the weights' values
         c = sl.sl_corrector_create(0)

@@ -249,9 +249,10 @@ int sl_batch_destroy(sl_batch *b);
  *                    that size is 0 (SL_CIR).
  *   workspace_bytes  its size.
  * The call allocates nothing and only enqueues kernels on stream (one per
- * interpolation call: 1 / 2 / 3 for CIR / FEC / BEC, 3 per axis for CEC).  A
- * non-finite or huge departure point sets SL_DEV_CFL and is replaced by the
- * arrival cell.
+ * interpolation call: 1 / 2 / 3 for CIR / FEC / BEC; for CEC one per axis
+ * when a line of the grid fits the fused sweep, else 3 per axis).  A
+ * non-finite Courant number, or one of magnitude 2^30 or more, sets SL_DEV_CFL
+ * and is replaced by 0 (the arrival cell).
  * Errors: those of sl_advect; SL_ERR_ARG for a workspace that is too small or
  * misaligned; SL_ERR_ALIAS when out, in, vel and workspace overlap (out and
  * workspace must each be disjoint from every other buffer).

@@ -37,30 +37,37 @@ struct WideGeo {
 };
 
 // Integer part and fraction of a displacement D (cell units): D = fl + f,
-// f in [0, 1).  A non-finite displacement, or one whose integer part a cell
-// index cannot hold, is flagged and replaced by 0 so that every index stays
-// in bounds.
+// f in [0, 1).  A non-finite displacement, or one of 2^30 cells or more, is
+// flagged and replaced by 0, so that every index below stays in 32 bits and
+// in bounds (grid sizes are at most 2^30).
 template <typename T>
-__device__ __forceinline__ int64_t floor_split(T D, T &f, bool &bad)
+__device__ __forceinline__ int floor_split(T D, T &f, bool &bad)
 {
-    if (!(fabs(D) < T(1.0e15))) {
+    if (!(fabs(D) < T(1073741824.0))) {
         bad = true;
         D = T(0);
     }
     const T fl = floor(D);
     f = D - fl;
-    return (int64_t)fl;
+    return (int)fl;
 }
 
-// v reduced into [0, n).  Departure points within one period of the grid take
-// a compare and an add; the 64-bit remainder (slow) only runs beyond that.
-__device__ __forceinline__ int wrap64(int64_t v, int n)
+// v reduced into [0, n), for v = a cell index (< n <= 2^30) plus an offset of
+// magnitude below 2^30, so v and v - n fit in 32 bits.  Departure points
+// within one period take a compare and an add; the remainder only runs beyond.
+__device__ __forceinline__ int wrapn(int v, int n)
 {
-    if (v >= 0 && v < n) return (int)v;
-    if (v < 0 && v >= -(int64_t)n) return (int)(v + n);
-    if (v >= n && v < 2 * (int64_t)n) return (int)(v - n);
-    int64_t r = v % n;
-    return (int)(r < 0 ? r + n : r);
+    if (v < 0) {
+        v += n;
+        if (v >= 0) return v;
+    } else if (v < n) {
+        return v;
+    } else {
+        v -= n;
+        if (v < n) return v;
+    }
+    const int r = v % n;
+    return r < 0 ? r + n : r;
 }
 
 __device__ __forceinline__ int64_t cell_at(const WideGeo &g, int x, int y, int z)
@@ -109,8 +116,8 @@ k_wide_interp(T *__restrict__ out, const T *__restrict__ src, const T *__restric
         for (int d = 0; d < 3; ++d) {
             const bool moves = AX < 0 ? d < NDIM : d == AX;
             if (moves) {
-                const int64_t fl = floor_split<T>(T(-dir) * C[k][d], f[d], bad);
-                b0[d] = wrap64((int64_t)pos[d] + fl, g.n[d]);
+                const int fl = floor_split<T>(T(-dir) * C[k][d], f[d], bad);
+                b0[d] = wrapn(pos[d] + fl, g.n[d]);
                 b1[d] = b0[d] + 1 == g.n[d] ? 0 : b0[d] + 1;
             }
         }
@@ -176,7 +183,7 @@ k_wide_cec(T *__restrict__ out, const T *__restrict__ lphi, const T *__restrict_
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         T c = C[k];
-        if (!(fabs(c) < T(1.0e15))) {
+        if (!(fabs(c) < T(1073741824.0))) {
             bad = true;
             c = T(0);
         }
@@ -185,8 +192,8 @@ k_wide_cec(T *__restrict__ out, const T *__restrict__ lphi, const T *__restrict_
         const int s = (r[k] > T(0)) - (r[k] < T(0));
         const int pos[3] = {x, y0 + k, z};
         int qj[3] = {pos[0], pos[1], pos[2]}, qu[3] = {pos[0], pos[1], pos[2]};
-        qj[AX] = wrap64((int64_t)pos[AX] - (int64_t)m, g.n[AX]);
-        qu[AX] = wrap64((int64_t)pos[AX] - (int64_t)m - s, g.n[AX]);
+        qj[AX] = wrapn(pos[AX] - (int)m, g.n[AX]);
+        qu[AX] = wrapn(pos[AX] - (int)m - s, g.n[AX]);
         dj[k] = on[k] ? delta[cell_at(g, qj[0], qj[1], qj[2])] : T(0);
         du[k] = on[k] ? delta[cell_at(g, qu[0], qu[1], qu[2])] : T(0);
     }
@@ -265,7 +272,7 @@ k_wide_sweep(T *__restrict__ out, const T *__restrict__ src, const T *__restrict
 #pragma unroll
         for (int k = 0; k < B; ++k) {
             if (!ok[k]) continue;
-            if (!(fabs(c[k]) < T(1.0e15))) {
+            if (!(fabs(c[k]) < T(1073741824.0))) {
                 bad = true;
                 c[k] = T(0);
             }
@@ -304,7 +311,7 @@ k_wide_sweep(T *__restrict__ out, const T *__restrict__ src, const T *__restrict
     each([&](int w, int i) {                                          // L_U[Phi]
         T f;
         bool unused = false;
-        const int b0 = wrap64((int64_t)i + floor_split<T>(-V[sidx(w, i)], f, unused), n);
+        const int b0 = wrapn(i + floor_split<T>(-V[sidx(w, i)], f, unused), n);
         const int b1 = b0 + 1 == n ? 0 : b0 + 1;
         const T a = S[sidx(w, b0)], b = S[sidx(w, b1)];
         Lb[sidx(w, i)] = a + f * (b - a);
@@ -313,7 +320,7 @@ k_wide_sweep(T *__restrict__ out, const T *__restrict__ src, const T *__restrict
     each([&](int w, int i) {                                          // delta = Phi - L_{-U}[L_U[Phi]]
         T f;
         bool unused = false;
-        const int b0 = wrap64((int64_t)i + floor_split<T>(V[sidx(w, i)], f, unused), n);
+        const int b0 = wrapn(i + floor_split<T>(V[sidx(w, i)], f, unused), n);
         const int b1 = b0 + 1 == n ? 0 : b0 + 1;
         const T a = Lb[sidx(w, b0)], b = Lb[sidx(w, b1)];
         S[sidx(w, i)] = S[sidx(w, i)] - (a + f * (b - a));
@@ -322,7 +329,7 @@ k_wide_sweep(T *__restrict__ out, const T *__restrict__ src, const T *__restrict
     each([&](int w, int i) {                                          // departure-cell correction
         const T c = V[sidx(w, i)], m = trunc(c), r = c - m;
         const int sg = (r > T(0)) - (r < T(0));
-        const int j = wrap64((int64_t)i - (int64_t)m, n), ju = wrap64((int64_t)i - (int64_t)m - sg, n);
+        const int j = wrapn(i - (int)m, n), ju = wrapn(i - (int)m - sg, n);
         const T dj = S[sidx(w, j)], du = S[sidx(w, ju)];
         out[gidx(w, i)] = Lb[sidx(w, i)] + dj * T(0.5) + (T(1) + fabs(r)) * T(1.0 / 6.0) * (du - dj);
     });
