@@ -780,8 +780,18 @@ def large_cfl_measurement(torch, sl, stream, n=256, cfl=3.75, timed=20):
         nsteps, dt)
     local_err, local_s = round_trip(
         lambda y, x, h, k: sl.sl_advect(y, x, vel, 3, dims, sp, h, sl.CEC, sl.F32, k & 1, stream), 100, dt0)
+    unsplit = {}
+    for name in ("CIR", "FEC", "BEC"):          # non-local operator compositions, unfused gathers
+        code = getattr(sl, name)
+        need_u = sl.sl_advect_wide_workspace(3, dims, code, sl.F32)
+
+        def fu(k, code=code, need_u=need_u):
+            sl.sl_advect_wide(b, a, vel, 3, dims, sp, dt, code, sl.F32, k & 1, ws, need_u, stream)
+        fu(0)
+        msu = time_steps(torch, stream, fu, timed)
+        unsplit[name] = {"ms_per_step": msu, "gcell_s": n ** 3 / (msu * 1e-3) / 1e9}
     sl.sl_device_status(stream)
-    return {"grid": dims, "cfl": dt * 2.0 / sp[0], "steps_for_T": nsteps, "ms_per_step": ms,
+    return {"grid": dims, "cfl": dt * 2.0 / sp[0], "steps_for_T": nsteps, "ms_per_step": ms, "unsplit": unsplit,
             "gcell_s": n ** 3 / (ms * 1e-3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "peak_kind": kind, "bytes_per_cell": WIDE_CEC_BYTES_PER_CELL},

@@ -58,3 +58,21 @@ def test_binding_refuses_missing_library(tmp_path):
             _lib.load(str(tmp_path / "nope.so"))
     finally:
         _lib._lib = saved
+
+
+def test_wide_workspace_sizes_without_a_gpu(libpath):
+    """sl_advect_wide_workspace only does arithmetic on its arguments: the
+    number of intermediate fields per scheme (CIR 0, FEC 1, BEC 2, CEC 3 in 2D
+    and 4 in 3D), each rounded up to 256 bytes, and the argument errors."""
+    from paper_1606_06117_gb300 import _lib
+    _lib.load(libpath)
+    field32 = (10 * 12 * 14 * 4 + 255) // 256 * 256
+    for scheme, count in ((_lib.CIR, 0), (_lib.FEC, 1), (_lib.BEC, 2), (_lib.CEC, 4)):
+        assert _lib.sl_advect_wide_workspace(3, [10, 12, 14], scheme, _lib.F32) == count * field32
+    assert _lib.sl_advect_wide_workspace(2, [33, 7, 1], _lib.CEC, _lib.F64) == 3 * ((33 * 7 * 8 + 255) // 256 * 256)
+    with pytest.raises(_lib.SLError, match="SL_ERR_UNSUPPORTED"):
+        _lib.sl_advect_wide_workspace(3, [8, 8, 8], _lib.CEC, _lib.F32_D64)
+    with pytest.raises(_lib.SLError, match="SL_ERR_ARG"):
+        _lib.sl_advect_wide_workspace(3, [8, 8, 8], 7, _lib.F32)
+    with pytest.raises(_lib.SLError, match="SL_ERR_ARG"):
+        _lib.sl_advect_wide_workspace(2, [8, 8, 2], _lib.CIR, _lib.F32)

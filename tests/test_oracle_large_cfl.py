@@ -158,3 +158,14 @@ def test_local_stencils_beyond_cfl_one():
         assert peak("BEC", U) > 1.05, U
     for name in ("CIR", "FEC", "CEC_reading"):
         assert peak(name, 1.05) > 1.05, name
+
+
+@pytest.mark.parametrize("shape", [(29,), (9, 14), (5, 6, 7)])
+def test_large_cfl_cec_equals_the_local_cec_below_cfl_one(shape):
+    """With m = trunc(C) = 0 the departure cell is the arrival cell: the adopted
+    large-CFL CEC is the local CEC (R7) operation for operation, bit for bit."""
+    rng = np.random.default_rng(24)
+    phi = rng.standard_normal(shape)
+    c = rng.uniform(-0.99, 0.99, size=(len(shape),) + shape)
+    for parity in (0, 1):
+        assert np.array_equal(O.step(phi, c, O.CEC_SL, parity), O.step(phi, c, O.CEC, parity))
