@@ -67,7 +67,7 @@ typedef enum {
     SL_ERR_CFL = -3,         /* a Courant number exceeds 1 (host checks) */
     SL_ERR_CUDA = -4,        /* a CUDA runtime call failed               */
     SL_ERR_TIMEOUT = -5,     /* a bounded device wait ran out            */
-    SL_ERR_UNSUPPORTED = -6, /* valid request this build does not serve  */
+    SL_ERR_UNSUPPORTED = -6, /* valid request the library does not serve */
     SL_ERR_NOMEM = -7        /* device or host allocation failed         */
 } sl_status;
 
