@@ -421,8 +421,10 @@ cudaError_t run(int scheme, const void *in_v, void *out_v, const void *vel_v, in
     const T *in = static_cast<const T *>(in_v), *vel = static_cast<const T *>(vel_v);
     T *out = static_cast<T *>(out_v);
     const size_t fb = wide_field_bytes(g.ncell, sizeof(T));
-    T *w[4];
-    for (int k = 0; k < 4; ++k) w[k] = reinterpret_cast<T *>(static_cast<char *>(work) + k * fb);
+    // the scheme's workspace fields (wide_fields of them; none for CIR, whose
+    // workspace may be NULL)
+    T *w[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; k < wide_fields(scheme, ndim); ++k) w[k] = reinterpret_cast<T *>(static_cast<char *>(work) + k * fb);
     if (scheme != 3) return ndim == 3 ? unsplit<T, 3>(scheme, out, in, vel, w[0], w[1], g, st)
                                       : unsplit<T, 2>(scheme, out, in, vel, w[0], w[1], g, st);
     // split CEC: in -> w2 (-> w3) -> out

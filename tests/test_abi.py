@@ -76,3 +76,29 @@ def test_wide_workspace_sizes_without_a_gpu(libpath):
         _lib.sl_advect_wide_workspace(3, [8, 8, 8], 7, _lib.F32)
     with pytest.raises(_lib.SLError, match="SL_ERR_ARG"):
         _lib.sl_advect_wide_workspace(2, [8, 8, 2], _lib.CIR, _lib.F32)
+
+
+def test_wide_step_argument_checks_without_a_gpu(libpath):
+    """sl_advect_wide validates its arguments before any CUDA call, so the
+    host logic runs here with addresses that are never dereferenced."""
+    from paper_1606_06117_gb300 import _lib
+    _lib.load(libpath)
+    dims = [8, 8, 8]
+    sp = [1.0, 1.0, 1.0]
+    fb = 8 * 8 * 8 * 4
+    inp, out, vel = 0x100000, 0x200000, 0x300000
+    need = _lib.sl_advect_wide_workspace(3, dims, _lib.CEC, _lib.F32)
+    ws = 0x400000
+    cases = [
+        ((out, 0, vel, 3, dims, sp, 0.1, _lib.CEC, _lib.F32, 0, ws, need), "SL_ERR_ARG"),          # NULL input
+        ((out, inp, vel, 3, dims, sp, 0.1, _lib.CEC, _lib.F32, 0, ws, need - 1), "SL_ERR_ARG"),  # small workspace
+        ((out, inp, vel, 3, dims, sp, 0.1, _lib.CEC, _lib.F32, 0, 0, need), "SL_ERR_ARG"),       # NULL workspace
+        ((out, inp, vel, 3, dims, sp, 0.1, _lib.CEC, _lib.F32, 0, ws + 16, need), "SL_ERR_ARG"),  # misaligned
+        ((inp + fb // 2, inp, vel, 3, dims, sp, 0.1, _lib.CEC, _lib.F32, 0, ws, need), "SL_ERR_ALIAS"),
+        ((out, inp, vel, 3, dims, sp, 0.1, _lib.CEC, _lib.F32, 0, vel + 256, need), "SL_ERR_ALIAS"),
+        ((out, inp, vel, 2, [8, 70000, 1], sp, 0.1, _lib.CIR, _lib.F32, 0, 0, 0), "SL_ERR_UNSUPPORTED"),
+        ((out, inp, vel, 3, dims, [1.0, 0.0, 1.0], 0.1, _lib.CEC, _lib.F32, 0, ws, need), "SL_ERR_ARG"),
+    ]
+    for args, code in cases:
+        with pytest.raises(_lib.SLError, match=code):
+            _lib.sl_advect_wide(*args)
