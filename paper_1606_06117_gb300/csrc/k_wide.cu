@@ -250,10 +250,17 @@ k_wide_sweep(T *__restrict__ out, const T *__restrict__ src, const T *__restrict
     }
     auto sidx = [&](int w, int i) { return AX == 0 ? w * n + i : i * W + w; };
     auto gidx = [&](int w, int i) { return AX == 0 ? base + (int64_t)w * n + i : base + (int64_t)i * stride + w; };
+    // rows of a power-of-two length take one flat loop with shifts
+    const int lg = (n & (n - 1)) == 0 ? __ffs(n) - 1 : -1;
+    const int rows = AX == 0 ? (int)min((int64_t)W, nlines - row0) : W;
     auto each = [&](auto f) {
         if constexpr (AX == 0) {
-            for (int w = 0; w < W && row0 + w < nlines; ++w)
-                for (int i = tid; i < n; i += kSweepThreads) f(w, i);
+            if (lg >= 0) {
+                for (int e = tid; e < (rows << lg); e += kSweepThreads) f(e >> lg, e & (n - 1));
+            } else {
+                for (int w = 0; w < rows; ++w)
+                    for (int i = tid; i < n; i += kSweepThreads) f(w, i);
+            }
         } else {
             for (int e = tid; e < W * n; e += kSweepThreads) f(e % W, e / W);
         }
