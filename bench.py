@@ -400,7 +400,7 @@ def run_ours(args):
                   "back in 8 z slabs on three streams, and returns once the result is on the host)"}
 
     extras = {}
-    if not args.no_extras and rank == 0:
+    if not args.no_extras and world == 1:   # per-GPU figures; the same at every N
         extras = side_measurements(torch, sl, dev, stream, n, phi, vel, sp, dt)
         del a, b
         torch.cuda.empty_cache()
