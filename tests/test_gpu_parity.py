@@ -182,6 +182,18 @@ def test_host_buffers_in_z_slabs_equal_device_path(shape, parity):
         assert rel_l2(out.double().numpy(), oracle_step(phi, vel, sp, dt, "CEC", 0)) <= TOL["f32"]
 
 
+def test_host_buffers_in_z_slabs_from_pageable_memory():
+    """Pageable (not page-locked) host buffers take the same slab path; the
+    copies are then staged by the driver, the result is the same."""
+    shape = (96, 32, 64)
+    phi, vel, sp, dt = random_case(shape, seed=82, cmax=0.9)
+    dims = [shape[2], shape[1], shape[0]]
+    out = torch.empty(shape)
+    for parity in (0, 1):
+        sl.sl_advect_host(out, phi, vel, 3, dims, sp, dt, sl.CEC, sl.F32, parity)
+        assert torch.equal(out, sl.advect(phi.to(DEV), vel.to(DEV), dt, sp, "CEC", parity).cpu())
+
+
 def test_host_buffers_in_z_slabs_flag_courant_violations():
     """A violation in any slab, including the cells next to slab edges, sets
     the status bit of a host-buffer step."""
