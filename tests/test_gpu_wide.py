@@ -177,3 +177,36 @@ def test_non_finite_velocity_is_flagged_and_stays_in_bounds():
         torch.cuda.synchronize()
         assert sl.sl_device_status() & sl.DEV_CFL
         assert got.shape == phi.shape
+
+
+@pytest.mark.parametrize("parity", [0, 1])
+def test_full_size_sampled_parity_at_cfl_3_64(parity):
+    """The benchmark's large-CFL configuration (256^3 ABC flow, 32-mode field,
+    CFL 3.64, the fused line sweeps) checked on 120 sampled cells.  A split CEC
+    output reads Phi within 3 ceil(C) + 3 cells along each axis (L_U reaches
+    ceil(C) + 1, delta another ceil(C) + 1, the correction ceil(C) + 1 more), so
+    the oracle's step on the periodic window of radius 15 gives the full-grid
+    value at its centre."""
+    from gpu_helpers import sample_cells, windows
+    n = 256
+    shape = (n, n, n)
+    sp = [2 * math.pi / n] * 3
+    dt0 = 0.8 * sp[0] / 2.0
+    dt = 100 * dt0 / 22                                        # Courant numbers up to 3.64
+    phi = W.random_modes(shape, W.draw_modes(3, 32, 8, seed=0), device=DEV, dtype=torch.float32)
+    vel = W.abc_velocity(shape, device=DEV, dtype=torch.float32)
+    out = sl.advect_wide(phi, vel, dt, sp, "CEC", parity)
+    torch.cuda.synchronize()
+    assert sl.sl_device_status() == 0
+    cells = sample_cells(shape, 120, seed=31 + parity)
+    r = 15
+    wp = windows(phi, cells, r).cpu().double().numpy()
+    wv = windows(vel, cells, r).cpu().numpy()                  # float32, (3, n, 31, 31, 31)
+    s32 = np.float32(dt / sp[0])
+    ref = np.empty(len(cells))
+    for i in range(len(cells)):
+        c = np.stack([(wv[d, i] * s32).astype(np.float64) for d in range(3)])
+        assert np.abs(c).max() < 3.7
+        ref[i] = O.step(wp[i], c, O.CEC_SL, parity)[r, r, r]
+    got = out[cells[:, 2], cells[:, 1], cells[:, 0]].cpu().double().numpy()
+    assert rel_l2(got, ref) <= TOL["f32"]
