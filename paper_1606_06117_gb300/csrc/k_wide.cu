@@ -266,8 +266,9 @@ k_wide_sweep(T *__restrict__ out, const T *__restrict__ src, const T *__restrict
         }
     };
     // staging: each thread issues the loads of B elements before storing any,
-    // so that B global loads of Phi and B of u_AX are in flight at once
-    constexpr int B = 8;
+    // so that B global loads of Phi and B of u_AX are in flight at once (4
+    // measured fastest of 1, 2, 4, 8 and 16: more costs registers and CTAs)
+    constexpr int B = 4;
     auto stage = [&](const int (&w)[B], const int (&i)[B], const bool (&ok)[B]) {
         T a[B], c[B];
 #pragma unroll
