@@ -20,8 +20,8 @@
  *
  * CIR, FEC and BEC use the unsplit multilinear operator on all axes.  The
  * velocity is taken at the arrival cell; the departure point is the straight
- * backtrace x_i - u_i dt.  Every step is one fused kernel: one read of Phi and
- * u and one write of Phi per cell.
+ * backtrace x_i - u_i dt.  Every step of sl_advect is one fused kernel: one
+ * read of Phi and u and one write of Phi per cell.
  *
  * Conventions shared by all entry points
  *   - Fields are C-contiguous [z][y][x] arrays (x fastest) of dims[2] x dims[1]
@@ -32,6 +32,7 @@
  *     C_d = u_d dt / dx_d.  The schemes need |C_d| <= 1 (Table 1 stability);
  *     larger values are reported through the device status word (bit
  *     SL_DEV_CFL) and the result is then undefined but stays in bounds.
+ *     sl_advect_wide takes any Courant number (non-local interpolation).
  *   - Pointers are device pointers owned by the caller unless the entry point
  *     says otherwise.  out must not alias in (SL_ERR_ALIAS).
  *   - Calls are asynchronous on the given CUDA stream (NULL = legacy default
