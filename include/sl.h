@@ -73,7 +73,8 @@ typedef enum {
 } sl_status;
 
 /* Bits of the device status word (see sl_device_status). */
-#define SL_DEV_CFL 1u        /* some |C_d| > 1 was seen by a kernel */
+#define SL_DEV_CFL 1u        /* a kernel saw |C_d| > 1 (sl_advect), or a
+                                non-finite C_d or |C_d| >= 2^30 (sl_advect_wide) */
 #define SL_DEV_TIMEOUT 2u    /* a bounded device wait gave up       */
 
 /* Library version, major * 10000 + minor * 100 + patch. */
