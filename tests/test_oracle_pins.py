@@ -351,3 +351,23 @@ def test_norms():
     assert rms == pytest.approx(math.sqrt((0.25 + 1.0) / 4))
     assert linf == 1.0
     assert rel == pytest.approx(math.sqrt(1.25 / (1 + 6.25 + 9 + 16)))
+
+
+@pytest.mark.parametrize("U", [0.2, 0.37, 0.8])
+def test_bench_table1_coefficients_equal_the_fixture(U):
+    """The benchmark's resolution study divides by Table 1's leading
+    coefficients, written there as c * u dx^(alpha - 1) for u = 1, dt = U dx;
+    they equal the fixture's transcription of Table 1."""
+    import bench
+    me = GOLD["modified_equation"]
+    dx = 1.0 / 256
+    dt = U * dx
+    for name, (alpha, c) in bench.TABLE1_DECAY.items():
+        coeff = ev(me[name][str(alpha)], U=U, u=1.0, dx=dx, dt=dt)
+        # the decay rate of exp(i k x) is -Re(C_alpha (i k)^alpha), per k^alpha
+        decay = -(coeff * 1j ** alpha).real
+        assert decay / dx ** (alpha - 1) == pytest.approx(c(U), rel=1e-12), name
+    for name, c in bench.TABLE1_DRIFT.items():
+        coeff = ev(me[name]["3"], U=U, u=1.0, dx=dx, dt=dt)
+        # the phase drift of exp(i k x) is Im(C_3 (i k)^3) = -C_3 k^3
+        assert -coeff / dx ** 2 == pytest.approx(c(U), rel=1e-12), name
