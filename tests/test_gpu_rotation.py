@@ -41,3 +41,30 @@ def test_rotation_matches_oracle_and_ranks(n):
         assert rel_l2(gpu, ref) <= 1e-12 * nsteps, name
         err[name] = rel_l2(gpu, phi0.numpy())
     assert err["CEC"] < err["BEC"] < err["FEC"] < err["CIR"], err
+
+
+def test_rotation_orders_through_512():
+    """Orders of the error against the exact field as N doubles, 64 -> 512:
+    FEC and BEC approach 2 and CEC 3 (Sec. 5: the orders under variable
+    velocity are those of constant velocity); CIR is still pre-asymptotic at
+    this sigma but its error falls."""
+    errs = {name: [] for name, _ in SCHEMES}
+    sizes = (64, 128, 256, 512)
+    for n in sizes:
+        shape = (n, n)
+        phi0 = W.gaussian_unwrapped(shape, (0.25, 0.5), 0.05, device=DEV)
+        vel = W.rotation_velocity(shape, device=DEV)
+        dt, nsteps = W.dt_for_cfl(1.0, math.pi * n, 0.5)
+        sp = [1.0 / n, 1.0 / n, 1.0]
+        for name, _ in SCHEMES:
+            x, y = phi0.clone(), torch.empty_like(phi0)
+            for k in range(nsteps):
+                sl.sl_advect(y, x, vel, 2, [n, n, 1], sp, dt, getattr(sl, name), sl.F64, k & 1)
+                x, y = y, x
+            errs[name].append((torch.linalg.vector_norm(x - phi0) / torch.linalg.vector_norm(phi0)).item())
+    order = {name: [math.log2(e[i] / e[i + 1]) for i in range(len(e) - 1)] for name, e in errs.items()}
+    assert 1.8 < order["FEC"][-1] < 2.2 and 1.8 < order["BEC"][-1] < 2.2, order
+    assert 2.6 < order["CEC"][-1] < 3.3, order
+    assert all(o > 0.25 for o in order["CIR"]), order
+    for name, e in errs.items():
+        assert e[-1] < e[0], name
