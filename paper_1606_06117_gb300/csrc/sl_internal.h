@@ -78,8 +78,8 @@ struct FastInst {
 };
 // Input planes a fast launch reads below and above its output planes.
 constexpr int kFastHaloBelow = 6, kFastHaloAbove = 3;
-// Bytes of one instance's tensor maps (14 maps of 128 bytes, 64-byte aligned).
-constexpr size_t kFastMapsBytes = 14 * 128;
+// Bytes of one instance's tensor maps (22 maps of 128 bytes, 64-byte aligned).
+constexpr size_t kFastMapsBytes = 22 * 128;
 // Encodes the tensor maps of an instance into dst (host memory, kFastMapsBytes).
 cudaError_t fast_encode_maps(void *dst, const FastInst &f);
 bool fast_eligible(const int64_t dims[3], int ndim, int dtype, bool aligned);

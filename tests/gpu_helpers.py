@@ -7,6 +7,8 @@ import torch
 from oracle import oracle as O
 
 TOL = {"f32": 1e-5, "f32_d64": 1e-5, "f64": 1e-12}
+# cell-by-cell bound, as a fraction of max |oracle|
+EW = {"f32": 1e-5, "f32_d64": 1e-5, "f64": 1e-12}
 TORCH_DT = {"f32": torch.float32, "f32_d64": torch.float32, "f64": torch.float64}
 
 
@@ -37,6 +39,30 @@ def rel_l2(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def assert_parity(got, ref, dtype, what="", allowance=1.0):
+    """A GPU result against the oracle's: relative L2 <= TOL[dtype] and, cell by
+    cell, |got - ref| <= EW[dtype] * max |ref|, both times `allowance` (multi-step
+    runs).  The cell-by-cell bound catches a defect confined to a few cells (a seam
+    or halo error) that a global norm would average away; a failure names the worst
+    cell (its index in `ref`'s shape) and both values."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    assert got.shape == ref.shape, (what, got.shape, ref.shape)
+    err = rel_l2(got, ref)
+    diff = np.abs(got - ref)
+    if not np.all(np.isfinite(diff)):
+        k = int(np.argmax(~np.isfinite(diff).ravel()))
+        raise AssertionError(f"{what}: non-finite result at {np.unravel_index(k, diff.shape)}")
+    scale = max(float(np.abs(ref).max()), 1e-300)
+    k = int(np.argmax(diff))
+    worst = float(diff.ravel()[k]) / scale
+    ok = err <= allowance * TOL[dtype] and worst <= allowance * EW[dtype]
+    assert ok, (f"{what}: relative L2 {err:.3e} (bar {allowance * TOL[dtype]:.1e}); worst cell "
+                f"{np.unravel_index(k, diff.shape)} off by {worst:.3e} of max|oracle| (bar "
+                f"{allowance * EW[dtype]:.1e}): GPU {got.ravel()[k]!r}, oracle {ref.ravel()[k]!r}")
+    return err, worst
 
 
 def sample_cells(shape, n, seed):

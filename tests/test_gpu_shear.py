@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_helpers import TOL, rel_l2
+from gpu_helpers import assert_parity
 from oracle import oracle as O
 from paper_1606_06117_gb300 import _lib as sl
 from paper_1606_06117_gb300 import workloads as W
@@ -46,8 +46,8 @@ def test_patch_test_matches_the_oracle(scheme, dtype):
     got, vel, dt, nsteps = gpu_run(n, W.patch_indicator(), scheme, dtype)
     c = vel.double().cpu().numpy() * (dt * n)
     ref = O.run(W.on_grid((n, n), W.patch_indicator()).numpy(), c, O.SCHEMES[scheme], nsteps)
-    err = rel_l2(got.double().cpu().numpy(), ref)
-    assert err <= (1e-12 * nsteps if dtype == "f64" else 4 * TOL["f32"]), err
+    assert_parity(got.cpu().numpy(), ref, dtype, f"patch test {scheme} {dtype}",
+                  allowance=(nsteps if dtype == "f64" else 4))
 
 
 def test_patch_ranking_at_512():

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_helpers import TOL, rel_l2
+from gpu_helpers import TOL, assert_parity, rel_l2
 from oracle import oracle as O
 from paper_1606_06117_gb300 import _lib as sl
 from paper_1606_06117_gb300 import workloads as W
@@ -58,8 +58,8 @@ def test_one_step_matches_the_oracle(shape, scheme, dtype, cmax):
         got = sl.advect_wide(phi, vel, dt, sp, scheme, parity)
         torch.cuda.synchronize()
         assert sl.sl_device_status() == 0
-        err = rel_l2(got.double().cpu().numpy(), oracle_of(phi, courant, scheme, parity))
-        assert err <= TOL[dtype], (parity, err)
+        assert_parity(got.cpu().numpy(), oracle_of(phi, courant, scheme, parity), dtype,
+                      f"{scheme} {dtype} {shape} cmax {cmax} parity {parity}")
 
 
 @pytest.mark.parametrize("scheme", ["CIR", "FEC", "BEC", "CEC"])
@@ -209,4 +209,4 @@ def test_full_size_sampled_parity_at_cfl_3_64(parity):
         assert np.abs(c).max() < 3.7
         ref[i] = O.step(wp[i], c, O.CEC_SL, parity)[r, r, r]
     got = out[cells[:, 2], cells[:, 1], cells[:, 0]].cpu().double().numpy()
-    assert rel_l2(got, ref) <= TOL["f32"]
+    assert_parity(got, ref, "f32", f"CFL 3.64 parity {parity}, sampled cells")
