@@ -84,10 +84,14 @@ struct L1 {
     static __device__ __forceinline__ V k(float x) { return x; }
     static __device__ __forceinline__ V abs(V a) { return fabsf(a); }
     static __device__ __forceinline__ V neg(V a) { return -a; }
-    // by the sign of C (given as mC = -C): C > 0, C < 0, C == 0
-    static __device__ __forceinline__ V pick(V mc, V cpos, V cneg, V czero)
+    // the sign of C (given as mC = -C), and a choice by it: C > 0, C < 0, C == 0
+    struct Sg {
+        bool p, n;
+    };
+    static __device__ __forceinline__ Sg sgn(V mc) { return Sg{mc < 0.f, mc > 0.f}; }
+    static __device__ __forceinline__ V pick(const Sg &s, V cpos, V cneg, V czero)
     {
-        return mc < 0.f ? cpos : (mc > 0.f ? cneg : czero);
+        return s.p ? cpos : (s.n ? cneg : czero);
     }
 };
 
@@ -112,9 +116,13 @@ struct L2 {
     static __device__ __forceinline__ V k(float x) { return make_float2(x, x); }
     static __device__ __forceinline__ V abs(V a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
     static __device__ __forceinline__ V neg(V a) { return make_float2(-a.x, -a.y); }
-    static __device__ __forceinline__ V pick(V mc, V cpos, V cneg, V czero)
+    struct Sg {
+        L1::Sg x, y;
+    };
+    static __device__ __forceinline__ Sg sgn(V mc) { return Sg{L1::sgn(mc.x), L1::sgn(mc.y)}; }
+    static __device__ __forceinline__ V pick(const Sg &s, V cpos, V cneg, V czero)
     {
-        return make_float2(L1::pick(mc.x, cpos.x, cneg.x, czero.x), L1::pick(mc.y, cpos.y, cneg.y, czero.y));
+        return make_float2(L1::pick(s.x, cpos.x, cneg.x, czero.x), L1::pick(s.y, cpos.y, cneg.y, czero.y));
     }
 };
 
@@ -214,22 +222,25 @@ __device__ __forceinline__ void run_any(const typename O::V (&p)[R + 6], const t
                                         typename O::V (&o)[R])
 {
     using V = typename O::V;
+    typename O::Sg sg[R + 4];   // signs at offsets -2..R+1, each compared once
+#pragma unroll
+    for (int j = 0; j < R + 4; ++j) sg[j] = O::sgn(m[j]);
     V L[R + 4];   // offsets -2..R+1
 #pragma unroll
     for (int j = 0; j < R + 4; ++j) {
-        const V nb = O::pick(m[j], p[j], p[j + 2], p[j + 1]);            // Phi_{j - s_j}
+        const V nb = O::pick(sg[j], p[j], p[j + 2], p[j + 1]);           // Phi_{j - s_j}
         L[j] = O::fma(O::sub(O::k(1.f), O::abs(m[j])), O::sub(p[j + 1], nb), nb);
     }
     V d[R + 2];   // offsets -1..R: (Phi_j - L_j) - U_j (L_{j+s_j} - L_j)
 #pragma unroll
     for (int j = 0; j < R + 2; ++j) {
-        const V Ln = O::pick(m[j + 1], L[j + 2], L[j], L[j + 1]);
+        const V Ln = O::pick(sg[j + 1], L[j + 2], L[j], L[j + 1]);
         d[j] = O::fma(O::neg(O::abs(m[j + 1])), O::sub(Ln, L[j + 1]), O::sub(p[j + 2], L[j + 1]));
     }
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         const V w = O::fma(O::abs(m[i + 2]), O::k(1.f / 6.f), O::k(1.f / 6.f));
-        const V dn = O::pick(m[i + 2], d[i], d[i + 2], d[i + 1]);         // delta_{i - s_i}
+        const V dn = O::pick(sg[i + 2], d[i], d[i + 2], d[i + 1]);        // delta_{i - s_i}
         o[i] = O::fma(w, O::sub(dn, d[i + 1]), O::fma(O::k(0.5f), d[i + 1], L[i + 2]));
     }
 }
@@ -309,12 +320,13 @@ struct ZWin {
             const V w = O::fma(m[P], O::k(1.f / 6.f), O::k(1.f / 6.f));
             out = O::fma(w, O::sub(dn, d[P ^ 1]), O::fma(O::k(0.5f), d[P ^ 1], L[P]));
         } else {
-            const V nb = O::pick(mn, ph[P], phi, ph[P ^ 1]);
+            const typename O::Sg s1 = O::sgn(mn), s2 = O::sgn(m[P ^ 1]), s3 = O::sgn(m[P]);
+            const V nb = O::pick(s1, ph[P], phi, ph[P ^ 1]);
             Ln = O::fma(O::sub(O::k(1.f), O::abs(mn)), O::sub(ph[P ^ 1], nb), nb);
-            const V Lnb = O::pick(m[P ^ 1], Ln, L[P], L[P ^ 1]);
+            const V Lnb = O::pick(s2, Ln, L[P], L[P ^ 1]);
             dn = O::fma(O::neg(O::abs(m[P ^ 1])), O::sub(Lnb, L[P ^ 1]), O::sub(ph[P], L[P ^ 1]));
             const V w = O::fma(O::abs(m[P]), O::k(1.f / 6.f), O::k(1.f / 6.f));
-            const V dd = O::pick(m[P], d[P], dn, d[P ^ 1]);
+            const V dd = O::pick(s3, d[P], dn, d[P ^ 1]);
             out = O::fma(w, O::sub(dd, d[P ^ 1]), O::fma(O::k(0.5f), d[P ^ 1], L[P]));
         }
         ph[P] = phi;
@@ -349,6 +361,29 @@ __device__ __forceinline__ void push_all(ZWin<O> (&win)[N], const typename O::V 
 #pragma unroll
         for (int i = 0; i < N; ++i) out[i] = win[i].template push<P, 0>(phi[i], mn[i]);
     }
+}
+
+// One push of one pair window with its own warp vote (hist as in push_all).
+template <int P>
+__device__ __forceinline__ float2 push_voted(ZWin<L2> &w, float2 phi, float2 mn, unsigned &hist, float lo, float hi)
+{
+    const unsigned now = sign_bits(lo, hi);
+    const unsigned cls = __reduce_and_sync(0xffffffffu, now & hist & (hist >> 2));
+    hist = ((hist & 3u) << 2) | now;
+    if (cls == 1u) return w.template push<P, 1>(phi, mn);
+    if (cls == 2u) return w.template push<P, -1>(phi, mn);
+    return w.template push<P, 0>(phi, mn);
+}
+
+// One push of each of a thread's z,y,x window sets, each set voting on its
+// own (a warp's set k covers one compact patch of columns).
+template <int P>
+__device__ __forceinline__ void push_sets(ZWin<L2> (&win)[3], const float2 (&ph)[3], const float2 (&mz)[3],
+                                          float2 (&res)[3], unsigned (&hist)[3], const float (&lo)[3],
+                                          const float (&hi)[3])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) res[k] = push_voted<P>(win[k], ph[k], mz[k], hist[k], lo[k], hi[k]);
 }
 
 // ---------------------------------------------------------------- geometry
@@ -782,6 +817,22 @@ template <int NS>
 constexpr size_t smem() { return sizeof(float) * (NS * SLOT + 2 * SZ_Z + SZ_Y) + 128; }
 }  // namespace zyx
 
+// Row zr in [0, 38) and pair column zc in [0, 20) of z-window pair q: the
+// first 640 pairs form 20 blocks of 8 rows x 4 pairs (one warp's 32 lanes, so
+// that a warp's sign vote covers a compact 8 x 8 patch of columns); the last
+// 120 fill rows 32..37 row by row.
+__device__ __forceinline__ void zpair(int q, int &zr, int &zc)
+{
+    if (q < 640) {
+        const int b = q >> 5, l = q & 31;
+        zr = 8 * (b / 5) + (l >> 2);
+        zc = 4 * (b % 5) + (l & 3);
+    } else {
+        zr = 32 + (q - 640) / 20;
+        zc = (q - 640) % 20;
+    }
+}
+
 // One staged array of the z,y,x order: rows [-4, 32 + nb) in bands of 4, 32
 // and nb rows (40 floats wide, from x0 - 4), and at the seam the side buffer
 // rows [-8, 32 + nb) in bands of 8, 32 and nb.
@@ -894,13 +945,14 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
     bool tmo = false;
     int slot_seq = 0;
 
-    // z-window pairs q = tid + NT k: row zr = q / 20 (y = zr - 3), pair column
-    // zc = q % 20 (x = 2 zc - 4, 2 zc - 3); zst: z-swept store offset (-1: no pair)
+    // z-window pairs q = tid + NT k at row zr (y = zr - 3) and pair column zc
+    // (x = 2 zc - 4, 2 zc - 3); zst: z-swept store offset (-1: no pair)
     int zst[NZW];
 #pragma unroll
     for (int k = 0; k < NZW; ++k) {
-        const int q = tid + NT * k;
-        zst[k] = q < NZP ? (q / 20) * ZS + 2 * (q % 20) : -1;
+        int zr, zc;
+        zpair(tid + NT * k, zr, zc);
+        zst[k] = tid + NT * k < NZP ? zr * ZS + 2 * zc : -1;
     }
     // y items: lanes < 20 of warp wq, pair column lane (x = 2 lane - 4), rows
     // [yg, yg + 4); yo: z-swept row yg - 3 (index y + 3) and y-swept row yg
@@ -930,7 +982,9 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
         int zop[NZW];
 #pragma unroll
         for (int k = 0; k < NZW; ++k) {
-            const int q = tid + NT * k, zr = q / 20, zc = q % 20;
+            const int q = tid + NT * k;
+            int zr, zc;
+            zpair(q, zr, zc);
             const bool side = ((zc < 2 ? 1 : (zc >= 18 ? 2 : 0)) & edge) != 0;
             zop[k] = q >= NZP ? 0 : (side ? O_SP + 20 + 4 * zr + 2 * (zc & 1) : O_PHI + (zr + 1) * ZS + 2 * zc);
         }
@@ -945,7 +999,7 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
         ZWin<L2> win[NZW];
 #pragma unroll
         for (int k = 0; k < NZW; ++k) win[k].init();
-        unsigned zhist = 0;
+        unsigned zhist[NZW] = {0u, 0u, 0u};
 
         int zw = wrapz(pfirst, nz);
         {
@@ -975,24 +1029,22 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
             {
                 const float2 msz2 = make_float2(msz, msz);
                 float2 ph[NZW], mz[NZW], res[NZW];
-                float lo = 3.0e38f, hi = -3.0e38f;
+                float zlo[NZW], zhi[NZW];
 #pragma unroll
                 for (int k = 0; k < NZW; ++k) {
-                    if (k < NZW - 1 || zst[k] >= 0) {    // a thread's first two pairs always exist
-                        ph[k] = *reinterpret_cast<const float2 *>(sb + zop[k]);
-                        mz[k] = __fmul2_rn(*reinterpret_cast<const float2 *>(sb + zop[k] + DZ), msz2);
-                        lo = min3f(lo, mz[k].x, mz[k].y);
-                        hi = max3f(hi, mz[k].x, mz[k].y);
-                    } else {
-                        ph[k] = make_float2(0.f, 0.f);
-                        mz[k] = make_float2(0.f, 0.f);
-                    }
+                    // a thread's last pair may not exist: it repeats the first
+                    // (same signs, computed and discarded)
+                    const int o = (k < NZW - 1 || zst[k] >= 0) ? zop[k] : zop[0];
+                    ph[k] = *reinterpret_cast<const float2 *>(sb + o);
+                    mz[k] = __fmul2_rn(*reinterpret_cast<const float2 *>(sb + o + DZ), msz2);
+                    zlo[k] = fminf(mz[k].x, mz[k].y);
+                    zhi[k] = fmaxf(mz[k].x, mz[k].y);
                 }
-                bad |= (lo < -1.f) | (hi > 1.f);
+                bad |= (min3f(zlo[0], zlo[1], zlo[2]) < -1.f) | (max3f(zhi[0], zhi[1], zhi[2]) > 1.f);
                 if (P == 0)
-                    push_all<0, L2, NZW>(win, ph, mz, res, zhist, 0xffffffffu, lo, hi);
+                    push_sets<0>(win, ph, mz, res, zhist, zlo, zhi);
                 else
-                    push_all<1, L2, NZW>(win, ph, mz, res, zhist, 0xffffffffu, lo, hi);
+                    push_sets<1>(win, ph, mz, res, zhist, zlo, zhi);
 #pragma unroll
                 for (int k = 0; k < NZW; ++k)
                     if (k < NZW - 1 || zst[k] >= 0) *reinterpret_cast<float2 *>(sz + zst[k]) = res[k];
