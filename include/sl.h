@@ -106,9 +106,15 @@ int sl_advect(void *out, const void *in, const void *vel, int ndim,
 
 /*
  * The same step applied to nfields fields advected by one velocity (e.g. the
- * three velocity components and a scalar).  outs[f] = S[ins[f]].  Same
- * arguments and errors as sl_advect; every outs[f] must differ from every
- * ins[g].
+ * three velocity components and a scalar).  outs[f] = S[ins[f]], equal bit for
+ * bit to one sl_advect call per field.  Same arguments and errors as
+ * sl_advect; every outs[f] must differ from every ins[g] and from the other
+ * outs.  Since L_U is linear in Phi for a fixed velocity (Sec. 2), every field
+ * shares the departure points and CEC weights; an SL_CEC step in FP32 on the
+ * geometry of the persistent kernel (see sl_autotune) advances up to 4 fields
+ * per launch: the launch's CTAs form groups, one CTA per field, that walk the
+ * same (column tile, plane) sequence, so that a group's velocity reads can be
+ * served from L2 after the first one.
  */
 int sl_advect_multi(void *const *outs, const void *const *ins, int nfields,
                     const void *vel, int ndim, const int64_t dims[3],

@@ -483,8 +483,10 @@ enum {
     M_V44_8, M_V44_32, M_V44_3, M_V40_4, M_V40_32, M_V40_3, M_V40_2, M_V4_8, M_V4_32, M_V4_3, M_V4_2,
     M_V32_2, M_V32_32, NMAPS
 };
+constexpr int NFMAPS = M_F4_3 + 1;   // the field's maps come first
 struct FastMaps {
-    CUtensorMap m[NMAPS];
+    CUtensorMap m[NMAPS];                          // field 0 and the velocity
+    CUtensorMap fx[kFastFields - 1][NFMAPS];       // fields 1 .. nf-1
 };
 static_assert(sizeof(FastMaps) == kFastMapsBytes, "tensor map block size");
 
@@ -586,8 +588,8 @@ constexpr size_t smem() { return sizeof(float) * (NS * SLOT + 2 * SZ_X) + 128; }
 
 // Stages the bundle of plane pz (reduced modulo nz) for the x,y,z order into
 // slot sb: Phi, u_x and u_y at pz, u_z at pz - 1 (one thread).
-__device__ __forceinline__ void xyz_issue(float *sb, uint64_t *b, const CUtensorMap *m, int x0, int y0, int nx,
-                                          int ny, int nz, int pz, bool seam)
+__device__ __forceinline__ void xyz_issue(float *sb, uint64_t *b, const CUtensorMap *fm, const CUtensorMap *m,
+                                          int x0, int y0, int nx, int ny, int nz, int pz, bool seam)
 {
     using namespace xyz;
     const int yt = y0 - 8 < 0 ? y0 - 8 + ny : y0 - 8, yb = y0 + TY >= ny ? y0 + TY - ny : y0 + TY;
@@ -597,7 +599,7 @@ __device__ __forceinline__ void xyz_issue(float *sb, uint64_t *b, const CUtensor
     bar_arm(b, BYTES + (seam ? BYTES_SEAM : 0u));
     const Band3 fb{M_F44_8, M_F44_32, M_F44_3, M_F4_8, M_F4_32, M_F4_3, 3};
     const Band3 vb{M_V44_8, M_V44_32, M_V44_3, M_V4_8, M_V4_32, M_V4_3, 3};
-    stage_rows(sb + O_PHI, sb + O_SP, m, fb, x0, xs, yt, y0, yb, pz, seam, b);
+    stage_rows(sb + O_PHI, sb + O_SP, fm, fb, x0, xs, yt, y0, yb, pz, seam, b);
     stage_rows(sb + O_UX, sb + O_SX, m, vb, x0, xs, yt, y0, yb, pz, seam, b);
     tma3(sb + O_UY, &m[M_V32_2], x0, yt2, nz + pz, b);
     tma3(sb + O_UY + 2 * TX, &m[M_V32_32], x0, y0, nz + pz, b);
@@ -633,9 +635,11 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
 
     const int tid = threadIdx.x;
     const FastInst *tab = BATCH ? table : &one;
-    const int64_t G = gridDim.x;
-    int64_t w = total * blockIdx.x / G;
-    const int64_t wend = total * (blockIdx.x + 1) / G;
+    // CTA groups of nf (one field each) share one (tile, plane) sequence
+    const int nf = BATCH ? 1 : one.nf, fld = BATCH ? 0 : (int)(blockIdx.x % (unsigned)nf);
+    const int64_t G = gridDim.x / nf, gb = blockIdx.x / nf;
+    int64_t w = total * gb / G;
+    const int64_t wend = total * (gb + 1) / G;
     bool bad = false;
     int hint = 0;
     Seg sg;
@@ -667,6 +671,7 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
     while (next_seg(tab, ninst, w, wend, hint, (double)total / (double)G, sg)) {
         const FastInst &I = tab[sg.inst];
         const CUtensorMap *maps = BATCH ? static_cast<const FastMaps *>(I.maps)->m : one_maps.m;
+        const CUtensorMap *fmaps = fld == 0 ? maps : one_maps.fx[fld - 1];
         const int x0 = sg.tx * TX, y0 = sg.ty * TY, nz = I.nz;
         const int64_t plane_n = I.plane;
         const float msx = -I.sx, msy = -I.sy, msz = -I.sz;
@@ -675,11 +680,11 @@ k_cec_xyz_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
         Blocks bp, bu;
         bp.set(O_PHI + (xrow + 5) * PW, O_SP + 4 * (xrow + 5), xr, sl, sr);
         bu.set(O_UX + (xrow + 5) * PW, O_SX + 4 * (xrow + 5), xr, sl, sr);
-        float *const obase = I.out + (int64_t)(y0 + yr) * I.nx + x0 + 2 * cp;
+        float *const obase = (BATCH ? I.out : I.fout[fld]) + (int64_t)(y0 + yr) * I.nx + x0 + 2 * cp;
         const int onx = I.nx;
         auto issue = [&](int pz, int s) {
             if (tid == ISSUER && !tmo) {
-                xyz_issue(buf + s * SLOT, &bars[s], maps, x0, y0, I.nx, I.ny, nz, pz, seam);
+                xyz_issue(buf + s * SLOT, &bars[s], fmaps, maps, x0, y0, I.nx, I.ny, nz, pz, seam);
                 armed |= 1u << s;
             }
         };
@@ -852,8 +857,8 @@ __device__ __forceinline__ void stage40(float *dst, float *side, const CUtensorM
 
 // Stages the bundle of plane pz (reduced modulo nz) for the z,y,x order into
 // slot sb: Phi at pz, u_z at pz - 1, u_y and u_x at pz - 3 (one thread).
-__device__ __forceinline__ void zyx_issue(float *sb, uint64_t *b, const CUtensorMap *m, int x0, int y0, int nx,
-                                          int ny, int nz, int pz, bool seam)
+__device__ __forceinline__ void zyx_issue(float *sb, uint64_t *b, const CUtensorMap *fm, const CUtensorMap *m,
+                                          int x0, int y0, int nx, int ny, int nz, int pz, bool seam)
 {
     using namespace zyx;
     const int yt4 = y0 - 4 < 0 ? y0 - 4 + ny : y0 - 4, yt8 = y0 - 8 < 0 ? y0 - 8 + ny : y0 - 8;
@@ -862,7 +867,7 @@ __device__ __forceinline__ void zyx_issue(float *sb, uint64_t *b, const CUtensor
     const int pz3 = pz >= 3 ? pz - 3 : pz - 3 + nz;
     const int xs = x0 == 0 ? nx - 4 : 0;
     bar_arm(b, BYTES + (seam ? BYTES_SEAM : 0u));
-    stage40(sb + O_PHI, sb + O_SP, m, M_F40_4, M_F40_32, M_F40_3, M_F4_8, M_F4_32, M_F4_3, x0, xs, yt4, yt8, y0,
+    stage40(sb + O_PHI, sb + O_SP, fm, M_F40_4, M_F40_32, M_F40_3, M_F4_8, M_F4_32, M_F4_3, x0, xs, yt4, yt8, y0,
             yb, pz, seam, b);
     stage40(sb + O_UZ, sb + O_SZ, m, M_V40_4, M_V40_32, M_V40_3, M_V4_8, M_V4_32, M_V4_3, x0, xs, yt4, yt8, y0,
             yb, 2 * nz + pz1, seam, b);
@@ -928,9 +933,11 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
 
     const int tid = threadIdx.x, lane = tid & 31, wq = tid >> 5;
     const FastInst *tab = BATCH ? table : &one;
-    const int64_t G = gridDim.x;
-    int64_t w = total * blockIdx.x / G;
-    const int64_t wend = total * (blockIdx.x + 1) / G;
+    // CTA groups of nf (one field each) share one (tile, plane) sequence
+    const int nf = BATCH ? 1 : one.nf, fld = BATCH ? 0 : (int)(blockIdx.x % (unsigned)nf);
+    const int64_t G = gridDim.x / nf, gb = blockIdx.x / nf;
+    int64_t w = total * gb / G;
+    const int64_t wend = total * (gb + 1) / G;
     bool bad = false;
     int hint = 0;
     Seg sg;
@@ -965,6 +972,7 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
     while (next_seg(tab, ninst, w, wend, hint, (double)total / (double)G, sg)) {
         const FastInst &I = tab[sg.inst];
         const CUtensorMap *maps = BATCH ? static_cast<const FastMaps *>(I.maps)->m : one_maps.m;
+        const CUtensorMap *fmaps = fld == 0 ? maps : one_maps.fx[fld - 1];
         const int x0 = sg.tx * TX, y0 = sg.ty * TY, nz = I.nz;
         const int64_t plane_n = I.plane;
         const float msx = -I.sx, msy = -I.sy, msz = -I.sz;
@@ -973,7 +981,7 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
         const int edge = (sl ? 1 : 0) | (sr ? 2 : 0);
         auto issue = [&](int pz, int s) {
             if (tid == ISSUER && !tmo) {
-                zyx_issue(buf + s * SLOT, &bars[s], maps, x0, y0, I.nx, I.ny, nz, pz, seam);
+                zyx_issue(buf + s * SLOT, &bars[s], fmaps, maps, x0, y0, I.nx, I.ny, nz, pz, seam);
                 armed |= 1u << s;
             }
         };
@@ -994,7 +1002,7 @@ k_cec_zyx_fast(const __grid_constant__ FastInst one, const __grid_constant__ Fas
         const int uyo = yside ? O_SY + 24 + 4 * yg + 2 * (lane & 1) : O_UY + (yg + 2) * ZS + 2 * lane;
         Blocks3 bu;
         bu.set(O_UX + xrow * ZS, O_SX + 32 + 4 * xrow, xr, sl, sr);
-        float *const obase = I.out + (int64_t)(y0 + xrow) * I.nx + x0 + xr;
+        float *const obase = (BATCH ? I.out : I.fout[fld]) + (int64_t)(y0 + xrow) * I.nx + x0 + xr;
 
         ZWin<L2> win[NZW];
 #pragma unroll
@@ -1164,7 +1172,10 @@ cudaError_t go_fast(const FastInst &one, const FastMaps &maps, const FastInst *t
     cudaError_t e = prepare<ZYX, BATCH>(grid);
     if (e != cudaSuccess) return e;
     if (grid_req > 0) grid = grid_req;
+    const int nf = tab ? 1 : one.nf;
     if (grid > total) grid = (int)total;
+    grid = grid >= nf ? grid / nf * nf : nf;   // whole groups of nf CTAs
+    if (grid > total * nf) grid = (int)(total * nf);
     if (ZYX)
         k_cec_zyx_fast<BATCH, SL_ZYX_SLOTS>
             <<<grid, NT, zyx::smem<SL_ZYX_SLOTS>(), st>>>(one, maps, tab, ninst, total, status);
@@ -1199,8 +1210,9 @@ EncodeTiled encoder()
 #define SL_TMA_L2 CU_TENSOR_MAP_L2_PROMOTION_NONE   // measured: less DRAM traffic than 64-256 B promotion
 #endif
 
-// Encodes the box shapes of one instance: the field f.in as [nz][ny][nx] and
-// the velocity f.vel as [3 nz][ny][nx] (FP32, row stride nx, plane stride nx ny).
+// Encodes the box shapes of one instance: each field f.fin[i] as [nz][ny][nx]
+// and the velocity f.vel as [3 nz][ny][nx] (FP32, row stride nx, plane stride
+// nx ny).
 cudaError_t encode_maps(FastMaps &fm, const FastInst &f)
 {
     EncodeTiled enc = encoder();
@@ -1215,11 +1227,14 @@ cudaError_t encode_maps(FastMaps &fm, const FastInst &f)
         const cuuint64_t strides[2] = {(cuuint64_t)f.nx * sizeof(float), (cuuint64_t)f.plane * sizeof(float)};
         const cuuint32_t box[3] = {(cuuint32_t)shape[k][1], (cuuint32_t)shape[k][2], 1u};
         const cuuint32_t step[3] = {1u, 1u, 1u};
-        void *base = const_cast<float *>(v ? f.vel : f.in);
-        if (enc(&fm.m[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, step,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, SL_TMA_L2,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return cudaErrorInvalidValue;
+        for (int fi = 0; fi < (v ? 1 : f.nf); ++fi) {
+            void *base = const_cast<float *>(v ? f.vel : f.fin[fi]);
+            CUtensorMap *dst = fi == 0 ? &fm.m[k] : &fm.fx[fi - 1][k];
+            if (enc(dst, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, step,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, SL_TMA_L2,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return cudaErrorInvalidValue;
+        }
     }
     return cudaSuccess;
 }
@@ -1228,26 +1243,34 @@ cudaError_t encode_maps(FastMaps &fm, const FastInst &f)
 cudaError_t cached_maps(FastMaps &fm, const FastInst &f)
 {
     struct Entry {
-        const float *in = nullptr, *vel = nullptr;
-        int nx = 0, ny = 0, nz = 0;
+        const float *fin[kFastFields] = {};
+        const float *vel = nullptr;
+        int nx = 0, ny = 0, nz = 0, nf = 0;
         FastMaps maps;
     };
     static Entry cache[8];
     static int next = 0;
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
+    auto same = [&](const Entry &c) {
+        if (c.nf != f.nf || c.vel != f.vel || c.nx != f.nx || c.ny != f.ny || c.nz != f.nz || !c.fin[0]) return false;
+        for (int i = 0; i < f.nf; ++i)
+            if (c.fin[i] != f.fin[i]) return false;
+        return true;
+    };
     for (const Entry &c : cache)
-        if (c.in == f.in && c.vel == f.vel && c.nx == f.nx && c.ny == f.ny && c.nz == f.nz && c.in) {
+        if (same(c)) {
             fm = c.maps;
             return cudaSuccess;
         }
     Entry &c = cache[next];
     cudaError_t e = encode_maps(c.maps, f);
     if (e != cudaSuccess) {
-        c.in = nullptr;
+        c.fin[0] = nullptr;
         return e;
     }
-    c.in = f.in;
+    for (int i = 0; i < kFastFields; ++i) c.fin[i] = i < f.nf ? f.fin[i] : nullptr;
+    c.nf = f.nf;
     c.vel = f.vel;
     c.nx = f.nx;
     c.ny = f.ny;
@@ -1292,6 +1315,11 @@ void fast_fill(FastInst &f, const void *in, void *out, const void *vel, const in
     f.maps = nullptr;
     f.zb = 0;
     f.nzr = f.nz;
+    f.nf = 1;
+    for (int i = 0; i < kFastFields; ++i) {
+        f.fin[i] = i == 0 ? f.in : nullptr;
+        f.fout[i] = i == 0 ? f.out : nullptr;
+    }
 }
 
 cudaError_t launch_cec_fast(const FastInst &one, const FastInst *dev_table, int ninst, int64_t total, int parity,

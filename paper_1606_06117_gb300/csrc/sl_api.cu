@@ -254,9 +254,35 @@ int sl_advect_multi(void *const *outs, const void *const *ins, int nfields, cons
     }
     DevCtx *c = ctx_get();
     if (!c) return fail(SL_ERR_CUDA, "could not create the device context");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool aligned = aligned16(vel);
+    for (int f = 0; f < nfields; ++f) aligned = aligned && aligned16(ins[f]) && aligned16(outs[f]);
+    if (scheme == SL_CEC && fast_eligible(dims, ndim, dtype, aligned)) {
+        // groups of up to kFastFields fields per launch: the CTAs of a group
+        // share one velocity read through L2
+        Tuned tu;
+        {
+            std::lock_guard<std::mutex> lk(g_mu);
+            auto it = g_tuned.find(std::make_tuple(dims[0], dims[1], dims[2], dtype));
+            if (it != g_tuned.end()) tu = it->second;
+        }
+        for (int f0 = 0; f0 < nfields; f0 += kFastFields) {
+            const int nf = std::min(kFastFields, nfields - f0);
+            FastInst one;
+            fast_fill(one, ins[f0], outs[f0], vel, dims, s, 0);
+            one.nf = nf;
+            for (int i = 0; i < nf; ++i) {
+                one.fin[i] = static_cast<const float *>(ins[f0 + i]);
+                one.fout[i] = static_cast<float *>(outs[f0 + i]);
+            }
+            const cudaError_t e = launch_cec_fast(one, nullptr, 1, (int64_t)one.ntiles * one.nz, step_parity,
+                                                  c->status, tu.grid, st);
+            if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        }
+        return SL_OK;
+    }
     for (int f = 0; f < nfields; ++f) {
-        rc = launch_step(outs[f], ins[f], vel, ndim, dims, s, scheme, dtype, step_parity,
-                         static_cast<cudaStream_t>(stream), c);
+        rc = launch_step(outs[f], ins[f], vel, ndim, dims, s, scheme, dtype, step_parity, st, c);
         if (rc) return rc;
     }
     return SL_OK;

@@ -64,6 +64,10 @@ int default_tz(int dtype, int ndim, const int64_t dims[3]);
 // tiles; w0 numbers its first (column tile, plane) pair in a batch.  A launch
 // writes the output planes [zb, zb + nzr) (fast_fill: all nz planes) and reads
 // the input planes [zb - 6, zb + nzr + 3), taken modulo nz.
+// A single-instance launch may advance nf <= kFastFields fields with one
+// velocity: its CTAs form groups of nf that take the same (column tile, plane)
+// sequence, one field each, so the group's velocity reads are served from L2.
+constexpr int kFastFields = 4;
 struct FastInst {
     const float *in;
     float *out;
@@ -75,11 +79,15 @@ struct FastInst {
     int64_t w0;
     const void *maps;   // batched tables: device address of this instance's tensor maps
     int zb, nzr;        // output planes [zb, zb + nzr); 0 <= zb, 1 <= nzr, zb + nzr <= nz
+    int nf;             // fields (1 in batched tables); fin[0] = in, fout[0] = out
+    const float *fin[kFastFields];
+    float *fout[kFastFields];
 };
 // Input planes a fast launch reads below and above its output planes.
 constexpr int kFastHaloBelow = 6, kFastHaloAbove = 3;
-// Bytes of one instance's tensor maps (22 maps of 128 bytes, 64-byte aligned).
-constexpr size_t kFastMapsBytes = 22 * 128;
+// Bytes of one instance's tensor maps (22 maps of the first field and the
+// velocity, 9 for each further field; 128 bytes each, 64-byte aligned).
+constexpr size_t kFastMapsBytes = (22 + 9 * (kFastFields - 1)) * 128;
 // Encodes the tensor maps of an instance into dst (host memory, kFastMapsBytes).
 cudaError_t fast_encode_maps(void *dst, const FastInst &f);
 bool fast_eligible(const int64_t dims[3], int ndim, int dtype, bool aligned);

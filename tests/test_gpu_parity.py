@@ -147,6 +147,28 @@ def test_multi_field_equals_single_calls():
         assert torch.equal(o, sl.advect(f, v, dt, sp, "CEC", 1))
 
 
+@pytest.mark.parametrize("nfields", [1, 2, 3, 4, 6])
+@pytest.mark.parametrize("parity", [0, 1])
+def test_multi_field_launch_equals_single_calls(nfields, parity):
+    """On the persistent kernel's geometry one launch advances up to four fields
+    (groups of CTAs share the velocity reads); six fields take two launches.
+    Every field equals its single-field step bit for bit, and the first matches
+    the oracle cell by cell."""
+    shape = (40, 64, 96)
+    _, vel, sp, dt = random_case(shape, seed=90 + nfields, cmax=0.9)
+    v = vel.to(DEV)
+    fields = [torch.randn(shape, device=DEV) for _ in range(nfields)]
+    outs = [torch.empty_like(f) for f in fields]
+    sl.sl_device_status()
+    sl.sl_advect_multi(outs, fields, v, 3, [96, 64, 40], sp, dt, sl.CEC, sl.F32, parity)
+    torch.cuda.synchronize()
+    assert sl.sl_device_status() == 0
+    for f, o in zip(fields, outs):
+        assert torch.equal(o, sl.advect(f, v, dt, sp, "CEC", parity))
+    assert_parity(outs[0].cpu().numpy(), oracle_step(fields[0].cpu(), vel, sp, dt, "CEC", parity), "f32",
+                  f"multi-field {nfields} parity {parity}")
+
+
 def test_host_buffers_equal_device_path():
     shape = (16, 20, 24)
     phi, vel, sp, dt = random_case(shape, seed=9)
@@ -420,14 +442,17 @@ def test_fast_path_partitions_agree(parity):
 
 @pytest.mark.parametrize("parity", [0, 1])
 def test_deformation_512_sampled_parity(parity):
-    """The 512^3 time-reversing deformation flow of the four-field run, one multi-field
-    step at t = 0 (velocity components advected as fields), on sampled cells."""
+    """The 512^3 time-reversing deformation flow of the four-field run: one
+    multi-field step at t = 0 of the three velocity components and the
+    random-mode scalar (one launch for the four fields), every field against
+    the oracle on sampled cells."""
     n = 512
     shape = (n, n, n)
     vel = W.deformation_velocity(shape, device=DEV, dtype=torch.float32)
     sp = [1.0 / n] * 3
     dt = 0.8 * sp[0] / float(vel.abs().amax())
-    ins = [vel[0].clone(), vel[2].clone()]
+    scal = W.random_modes(shape, W.draw_modes(3, 32, 8, seed=5), length=1.0, device=DEV, dtype=torch.float32)
+    ins = [vel[0].clone(), vel[1].clone(), vel[2].clone(), scal]
     outs = [torch.empty_like(f) for f in ins]
     sl.sl_advect_multi(outs, ins, vel, 3, [n, n, n], sp, dt, sl.CEC, sl.F32, parity)
     torch.cuda.synchronize()
