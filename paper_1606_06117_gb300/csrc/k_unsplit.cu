@@ -19,23 +19,26 @@ namespace {
 
 // Multilinear value at a departure point with |C| <= 1 in the sign form of
 // Sec. 3: on each axis the corners are the cell itself and its neighbour at
-// offset `o_d` (= -s_d for L_U, +s_d for L_{-U}), weighted 1 - U_d and U_d.
-// q0 is the cell's plane, q1 the neighbouring plane on z.
+// offset `o_d` (= -s_d for L_U, +s_d for L_{-U}; 0 when C_d = 0), weighted
+// W_d = 1 - U_d and U_d.  Each lerp is written from the neighbour, n + W (c - n),
+// so that U = 1 picks the neighbour exactly, C = 0 (o_d = 0) the cell, and a
+// constant field stays constant.  q0 is the cell's plane, q1 the neighbouring
+// plane on z (q0 itself when C_z = 0); wx, wy, wz are the W_d.
 template <typename A, bool HAS_Z, typename S>
-__device__ __forceinline__ A mlerp(const S *q0, const S *q1, int o, int ox, int oy, A ux, A uy, A uz)
+__device__ __forceinline__ A mlerp(const S *q0, const S *q1, int o, int ox, int oy, A wx, A wy, A wz)
 {
     const A a00 = A(q0[o]), a10 = A(q0[o + ox]), a01 = A(q0[o + oy]), a11 = A(q0[o + oy + ox]);
-    const A b0 = a00 + ux * (a10 - a00);
-    const A b1 = a01 + ux * (a11 - a01);
-    const A c0 = b0 + uy * (b1 - b0);
+    const A b0 = a10 + wx * (a00 - a10);
+    const A b1 = a11 + wx * (a01 - a11);
+    const A c0 = b1 + wy * (b0 - b1);
     if constexpr (!HAS_Z) {
         return c0;
     } else {
         const A e00 = A(q1[o]), e10 = A(q1[o + ox]), e01 = A(q1[o + oy]), e11 = A(q1[o + oy + ox]);
-        const A f0 = e00 + ux * (e10 - e00);
-        const A f1 = e01 + ux * (e11 - e01);
-        const A c1 = f0 + uy * (f1 - f0);
-        return c0 + uz * (c1 - c0);
+        const A f0 = e10 + wx * (e00 - e10);
+        const A f1 = e11 + wx * (e01 - e11);
+        const A c1 = f1 + wy * (f0 - f1);
+        return c1 + wz * (c0 - c1);
     }
 }
 
@@ -237,9 +240,10 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
                     const int o = (yy - h + H) * PW + (xx - h + 4);
                     const D cx = D(cP[o]) * sxd, cy = D(cP[SC + o]) * syd;
                     const D cz = HAS_Z ? D(cP[2 * SC + o]) * szd : D(0);
-                    const int ox = cx > D(0) ? -1 : 1, oy = cy > D(0) ? -PW : PW;
-                    const T *phi1 = HAS_Z ? (cz > D(0) ? sl_phi(q - 1) : sl_phi(q + 1)) : phi0;
-                    const D v = mlerp<D, HAS_Z>(phi0, phi1, o, ox, oy, fabs(cx), fabs(cy), fabs(cz));
+                    const int ox = by_sign(cx, -1, 1, 0), oy = by_sign(cy, -PW, PW, 0);
+                    const T *phi1 = HAS_Z ? by_sign<D, const T *>(cz, sl_phi(q - 1), sl_phi(q + 1), phi0) : phi0;
+                    const D v = mlerp<D, HAS_Z>(phi0, phi1, o, ox, oy, D(1) - fabs(cx), D(1) - fabs(cy),
+                                                D(1) - fabs(cz));
                     if constexpr (NST == 1) {
                         bad |= fabs(cx) > D(1) || fabs(cy) > D(1) || fabs(cz) > D(1);
                         const int gx = x0 + xx, gy = y0 + yy;
@@ -265,9 +269,10 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
                         const D cx = D(cP[o]) * sxd, cy = D(cP[SC + o]) * syd;
                         const D cz = HAS_Z ? D(cP[2 * SC + o]) * szd : D(0);
                         // reversed flow: departure x + u dt, corners toward +s
-                        const int ox = cx > D(0) ? 1 : -1, oy = cy > D(0) ? PW : -PW;
-                        const D *l1 = HAS_Z ? (cz > D(0) ? sl_l(q + 1) : sl_l(q - 1)) : l0;
-                        const D bar = mlerp<D, HAS_Z>(l0, l1, o, ox, oy, fabs(cx), fabs(cy), fabs(cz));
+                        const int ox = by_sign(cx, 1, -1, 0), oy = by_sign(cy, PW, -PW, 0);
+                        const D *l1 = HAS_Z ? by_sign<D, const D *>(cz, sl_l(q + 1), sl_l(q - 1), l0) : l0;
+                        const D bar = mlerp<D, HAS_Z>(l0, l1, o, ox, oy, D(1) - fabs(cx), D(1) - fabs(cy),
+                                                      D(1) - fabs(cz));
                         const D delta = D(phiq[o]) - bar;
                         if constexpr (NST == 2) {
                             bad |= fabs(cx) > D(1) || fabs(cy) > D(1) || fabs(cz) > D(1);
@@ -293,9 +298,10 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
                         const T cx = T(D(cP[o]) * sxd), cy = T(D(cP[SC + o]) * syd);
                         const T cz = HAS_Z ? T(D(cP[2 * SC + o]) * szd) : T(0);
                         bad |= fabs(cx) > T(1) || fabs(cy) > T(1) || fabs(cz) > T(1);
-                        const int ox = cx > T(0) ? -1 : 1, oy = cy > T(0) ? -PW : PW;
-                        const T *p1 = HAS_Z ? (cz > T(0) ? sl_p(q - 1) : sl_p(q + 1)) : p0;
-                        const T v = mlerp<T, HAS_Z>(p0, p1, o, ox, oy, fabs(cx), fabs(cy), fabs(cz));
+                        const int ox = by_sign(cx, -1, 1, 0), oy = by_sign(cy, -PW, PW, 0);
+                        const T *p1 = HAS_Z ? by_sign<T, const T *>(cz, sl_p(q - 1), sl_p(q + 1), p0) : p0;
+                        const T v = mlerp<T, HAS_Z>(p0, p1, o, ox, oy, T(1) - fabs(cx), T(1) - fabs(cy),
+                                                    T(1) - fabs(cz));
                         const int gx = x0 + xx, gy = y0 + yy;
                         if (gx < g.nx && gy < g.ny) out[(int64_t)(q >= g.nz ? q - g.nz : q) * g.plane + (int64_t)gy * g.nx + gx] = v;
                     }

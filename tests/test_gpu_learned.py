@@ -190,3 +190,72 @@ def test_learned_rejects_unsupported_grids():
         assert e.value.code == -6 and "aligned" in str(e.value)
     finally:
         sl.sl_corrector_destroy(c)
+
+
+def _trained_corrector(shape=(64, 64, 64), iters=400, seed=5):
+    """A corrector trained on pairs of plain CEC steps of an ABC / random-mode field."""
+    dims = [shape[2], shape[1], shape[0]]
+    sp = [2 * math.pi / n for n in dims]
+    vel = W.abc_velocity(shape, device=DEV, dtype=torch.float32)
+    dt = 0.8 * min(sp) / 2.0
+    c = sl.sl_corrector_create(seed)
+    cur = W.random_modes(shape, W.draw_modes(3, 16, 4, seed=seed), device=DEV, dtype=torch.float32)
+    for k in range(3):
+        nxt = sl.advect(cur, vel, dt, sp, "CEC", 0)
+        sl.sl_corrector_add_samples(c, cur, nxt, vel, dims, sp, dt, 60000, seed=200 + k)
+        cur = sl.advect(cur, vel, dt, sp, "CEC", k)
+    sl.sl_corrector_train(c, iters, 2048, 2e-3, seed=3)
+    return c, cur, vel, dims, sp, dt
+
+
+def test_learned_step_error_is_measured_against_the_oracle():
+    """The check judges the learned step by its distance from the plain
+    third-order step computed on the GPU.  On sampled cells, the FP64 oracle's
+    step gives the same distance to within the GPU step's own error against the
+    oracle (FP32 rounding), so the check is a judgement against the oracle; the
+    two errors are reported beside each other."""
+    from gpu_helpers import oracle_at_cells, rel_l2, sample_cells
+    c, cur, vel, dims, sp, dt = _trained_corrector()
+    try:
+        shape = tuple(cur.shape)
+        learned = torch.empty_like(cur)
+        used, errs = sl.sl_advect_learned(c, learned, cur, vel, 3, dims, sp, dt, 0, check=0)
+        assert used == 0
+        plain = sl.advect(cur, vel, dt, sp, "CEC", 0)
+        cells = sample_cells(shape, 800, seed=7)
+        ref = oracle_at_cells(cur, vel, sp, dt, "CEC", 0, cells)
+        at = lambda t: t[cells[:, 2], cells[:, 1], cells[:, 0]].cpu().double().numpy()
+        plain_vs_oracle = rel_l2(at(plain), ref)
+        learned_vs_oracle = rel_l2(at(learned), ref)
+        learned_vs_plain = rel_l2(at(learned), at(plain))
+        print(f"learned vs oracle {learned_vs_oracle:.3e}, plain CEC vs oracle {plain_vs_oracle:.3e}")
+        assert plain_vs_oracle <= 1e-5
+        assert abs(learned_vs_oracle - learned_vs_plain) <= plain_vs_oracle + 1e-7
+        # the checked step's learned error (whole field, against the GPU step)
+        used, errs = sl.sl_advect_learned(c, torch.empty_like(cur), cur, vel, 3, dims, sp, dt, 0, check=1,
+                                          fallback_ratio=1e9)
+        assert used == 0 and abs(errs[0] - learned_vs_plain) <= 0.5 * learned_vs_plain
+    finally:
+        sl.sl_corrector_destroy(c)
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_corrupted_weights_fall_back_to_the_plain_step(bad):
+    """Host-side fault injection: a non-finite weight written through
+    sl_corrector_set_params makes the next checked step hand out the plain CEC
+    step and keeps the corrector on the plain scheme until reset."""
+    c, cur, vel, dims, sp, dt = _trained_corrector(iters=50)
+    try:
+        params = np.empty(sl.sl_corrector_param_count(), dtype=np.float32)
+        params[:] = sl.sl_corrector_get_params(c)
+        params[5] = bad                                   # one entry of W1
+        sl.sl_corrector_set_params(c, params)
+        out = torch.empty_like(cur)
+        used, errs = sl.sl_advect_learned(c, out, cur, vel, 3, dims, sp, dt, 1, check=1, fallback_ratio=2.0)
+        assert used == 1
+        assert torch.equal(out, sl.advect(cur, vel, dt, sp, "CEC", 1))
+        used, _ = sl.sl_advect_learned(c, out, cur, vel, 3, dims, sp, dt, 0)
+        assert used == 1 and torch.equal(out, sl.advect(cur, vel, dt, sp, "CEC", 0))
+        assert torch.isfinite(out).all()
+    finally:
+        sl.sl_corrector_destroy(c)

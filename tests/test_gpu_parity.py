@@ -74,16 +74,21 @@ def test_constant_field_is_preserved_bitwise(scheme, dtype):
         assert torch.equal(out, phi)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64", "f32_d64"])
+@pytest.mark.parametrize("shape", [(8, 12, 16), (16, 32, 64)])   # generic kernels; the persistent CEC kernel
 @pytest.mark.parametrize("scheme", SCHEMES)
-def test_integer_courant_is_a_shift(scheme):
-    shape = (8, 12, 16)
+def test_integer_courant_is_a_shift(scheme, shape, dtype):
+    """Pin P2: Courant numbers of +-1 on every axis (and 0 on one) give the exact
+    cyclic shift, bit for bit, in every scheme and both sweep orders."""
     rng = np.random.default_rng(4)
-    phi = torch.from_numpy(rng.standard_normal(shape)).float()
+    t = TORCH_DT[dtype]
+    phi = torch.from_numpy(rng.standard_normal(shape)).to(t)
     sp, dt = [1.0, 1.0, 1.0], 1.0
-    vel = torch.stack([torch.full(shape, v) for v in (1.0, -1.0, 1.0)]).float()
-    out = gpu_step(phi, vel, sp, dt, scheme, 0, "f32").cpu()
-    ref = torch.roll(phi, shifts=(1, -1, 1), dims=(0, 1, 2))
-    assert torch.allclose(out, ref, atol=1e-6, rtol=0)
+    for c, shifts in (((1.0, -1.0, 1.0), (1, -1, 1)), ((-1.0, 0.0, -1.0), (-1, 0, -1))):
+        vel = torch.stack([torch.full(shape, v) for v in c]).to(t)
+        for parity in ((0, 1) if scheme == "CEC" else (0,)):
+            out = gpu_step(phi, vel, sp, dt, scheme, parity, dtype).cpu()
+            assert torch.equal(out, torch.roll(phi, shifts=shifts, dims=(0, 1, 2))), (c, parity)
 
 
 def test_courant_violation_sets_status_bit():
