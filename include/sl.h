@@ -178,7 +178,11 @@ int sl_norms(const void *a, const void *b, int64_t n, int dtype, double out[3],
  *
  * The first call on a device resolves the array's device address (once per
  * device, with that device current); make that first call before any stream
- * capture.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ * capture.  The resolved address is kept for the life of the process: after a
+ * device reset (cudaDeviceReset, or the primary context torn down and made
+ * again) it no longer points at mapped memory, so do not call this function on
+ * that device after such a reset.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
  * n must be in [1, 2^40]; larger or smaller values return SL_ERR_ARG.  All calls
  * share the one array: calls whose kernels overlap on the GPU (e.g. on two
  * streams at once) race and may return wrong norms; serialise them.

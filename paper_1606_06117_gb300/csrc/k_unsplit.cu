@@ -370,6 +370,8 @@ cudaError_t by_shape(int scheme, bool has_z, bool vec, const Geo &g, int grid, c
 cudaError_t launch_unsplit(int dtype, int scheme, const void *in, void *out, const void *vel, int ndim,
                            const int64_t dims[3], const double s[3], Launch lc, unsigned *status, cudaStream_t st)
 {
+    if (scheme == 0 && cir_fast_eligible(dtype, ndim, dims, lc.aligned))
+        return launch_cir_fast(in, out, vel, dims, s, lc, status, st);
     Geo g;
     g.nx = (int)dims[0];
     g.ny = (int)dims[1];

@@ -36,6 +36,11 @@ cudaError_t launch_split_cec(int dtype, const void *in, void *out, const void *v
 cudaError_t launch_unsplit(int dtype, int scheme, const void *in, void *out, const void *vel,
                            int ndim, const int64_t dims[3], const double s[3], Launch lc,
                            unsigned *status, cudaStream_t st);
+// FP32 3D CIR kernel on four-cell groups (k_cir_fast.cu); launch_unsplit routes
+// eligible CIR steps to it.
+bool cir_fast_eligible(int dtype, int ndim, const int64_t dims[3], bool aligned);
+cudaError_t launch_cir_fast(const void *in, void *out, const void *vel, const int64_t dims[3], const double s[3],
+                            Launch lc, unsigned *status, cudaStream_t st);
 
 // Reductions (synchronous results through host pointers after a stream sync).
 cudaError_t launch_norms(int dtype, const void *a, const void *b, int64_t n, double *partials,
