@@ -205,6 +205,44 @@ int sl_selftest_wait_timeout(unsigned polls, void *stream);
  */
 int sl_device_status(void *stream, unsigned *out_bits);
 
+/*
+ * Autotuning of launch shapes (no counterpart in the paper).
+ *
+ * The kernel that serves a step is fixed by the request (scheme, dtype,
+ * dimensionality, sizes, 16-byte alignment); the autotuner chooses, by timing
+ * on the caller's buffers, among launch shapes of that kernel that change only
+ * how cells are grouped into work, never a cell's arithmetic, so every choice
+ * gives bitwise the same results:
+ *   SL_KERNEL_CEC_FAST     persistent FP32 split CEC kernel (32 x 32 column
+ *                          tiles): CTAs per SM, 1 or 2.
+ *   SL_KERNEL_CEC_SPLIT    generic split CEC kernel: planes per work item.
+ *   SL_KERNEL_CIR_GROUPS   FP32 CIR kernel on four-cell groups: tile height
+ *                          16 or 32, planes per work item.
+ *   SL_KERNEL_UNSPLIT      generic CIR / FEC / BEC kernel: tile height 8, 16 or
+ *                          32 (FP32 3D grids with dims[0] % 4 == 0 and aligned
+ *                          buffers; otherwise the dtype's fixed height) and
+ *                          planes per work item, or for 3D BEC (persistent
+ *                          equal shares) CTAs per SM, 1 to 3.
+ * A choice is cached per (dims, scheme, dtype) in the process and used by
+ * sl_advect, sl_advect_multi, sl_advect_host and sl_batch_create whenever the
+ * request is served by the kernel it was tuned for.
+ */
+enum {
+    SL_KERNEL_CEC_FAST = 1,
+    SL_KERNEL_CEC_SPLIT = 2,
+    SL_KERNEL_CIR_GROUPS = 3,
+    SL_KERNEL_UNSPLIT = 4
+};
+
+typedef struct {
+    int kernel;       /* SL_KERNEL_*                                         */
+    int tile_x;       /* column tile of a work item, cells along x           */
+    int tile_y;       /*                             cells along y           */
+    int tile_z;       /* planes per work item; 0: persistent equal shares    */
+    int ctas_per_sm;  /* CTAs per SM of a persistent launch; 0: one per item  */
+    float ms;         /* measured time of one step, milliseconds             */
+} sl_tuning;
+
 /* --------------------------------------------------------------------------
  * Batched advection of independent periodic 3D problems of uneven sizes in one
  * persistent launch per step (no counterpart in the paper: a throughput form
@@ -224,10 +262,25 @@ typedef struct sl_batch sl_batch;
 /*
  * Build a batch plan for n instances (copied; the device pointers must stay
  * valid while the plan is used).  The plan owns a device instance table and a
- * work counter.  tile_z is the z extent of one work item (0 = autotuned).
+ * work counter.  When every instance fits the persistent FP32 CEC kernel (see
+ * sl_autotune) the plan launches it over all instances; otherwise a generic
+ * work-queue kernel whose items are (column tile, z chunk) pairs.  tile_z is
+ * the z extent of one such item; 0 takes, per instance, the planes per work
+ * item cached by sl_autotune_scheme for (its dims, SL_CEC, dtype) on the
+ * generic split kernel, else 32.
  */
 int sl_batch_create(sl_batch **out, const sl_instance *inst, int n, int scheme,
                     int dtype, int tile_z);
+/*
+ * Time the plan's candidate CTA counts (1, 2 or 4 CTAs per SM, within the
+ * kernel's occupancy) on even steps and keep the fastest in the plan; *best
+ * (may be NULL) receives the choice, with kernel SL_KERNEL_CEC_FAST or
+ * SL_KERNEL_CEC_SPLIT and the plan's tile.  Every instance's B buffer is
+ * overwritten (A is only read).  Results of later steps are bitwise those of
+ * the untuned plan.  sl_batch_tuning reports the plan's current launch shape.
+ */
+int sl_batch_autotune(sl_batch *b, sl_tuning *best, void *stream);
+int sl_batch_tuning(const sl_batch *b, sl_tuning *out);
 /*
  * One step of every instance: even step_index reads A and writes B with sweep
  * order x,y,z; odd step_index reads B and writes A with order z,y,x.  Only a
@@ -276,14 +329,42 @@ int sl_advect_wide(void *out, const void *in, const void *vel, int ndim,
                    int64_t workspace_bytes, void *stream);
 
 /*
- * Autotune: time the candidate launch shapes of the fused SL_CEC kernel for
- * this grid on the given stream (device buffers supplied by the caller; the
- * step is run several times, so out is overwritten) and cache the fastest for
- * later calls with the same (dims, dtype).  The candidates are z extents of a
- * work item for the generic kernel, or CTA counts (one or two waves of CTAs
- * per SM) for the persistent FP32 kernel used when dims[0] and dims[1] are
- * multiples of 32 (dims[0] >= 64, dims[2] >= 8) and the buffers are 16-byte
- * aligned.  The chosen value is returned in *tile_z.
+ * Time every candidate launch shape of the kernel serving (scheme, dtype,
+ * ndim, dims, alignment of the buffers) on the given stream, cache the
+ * fastest and return it in *best (may be NULL).  The buffers are the caller's
+ * device memory, laid out as for sl_advect; out is overwritten (each candidate
+ * runs a few steps, both sweep orders for SL_CEC), in and vel are only read.
+ * Errors: those of sl_advect.
+ */
+int sl_autotune_scheme(void *out, const void *in, const void *vel, int ndim,
+                       const int64_t dims[3], const double spacing[3], double dt,
+                       int scheme, int dtype, sl_tuning *best, void *stream);
+
+/*
+ * The cached choice for (dims, scheme, dtype) in *out: SL_OK, or SL_ERR_ARG
+ * when nothing is cached.
+ */
+int sl_tuning_get(const int64_t dims[3], int scheme, int dtype, sl_tuning *out);
+
+/*
+ * Write every cached choice to the text file at path (one line per entry:
+ * nx ny nz scheme dtype kernel tile_x tile_y tile_z ctas_per_sm ms, after a
+ * comment line naming the device), or read such a file back into the cache
+ * (entries replace cached ones with the same key).  A choice depends on the GPU
+ * model that timed it; load only files written on the same model.  Errors:
+ * SL_ERR_ARG (NULL path, unreadable / unwritable file, or a malformed line:
+ * nothing of the file is loaded then).  sl_tuning_clear empties the cache.
+ */
+int sl_tuning_save(const char *path);
+int sl_tuning_load(const char *path);
+int sl_tuning_clear(void);
+
+/*
+ * Former interface, kept: sl_autotune_scheme for SL_CEC; *tile_z receives the
+ * chosen planes per work item of the generic kernel, or the chosen CTA count
+ * (CTAs per SM times SMs) of the persistent FP32 kernel (used when dims[0] and
+ * dims[1] are multiples of 32, dims[0] >= 64, dims[2] >= 8 and the buffers are
+ * 16-byte aligned).
  */
 int sl_autotune(void *out, const void *in, const void *vel, int ndim,
                 const int64_t dims[3], const double spacing[3], double dt,

@@ -33,13 +33,25 @@ EXPORTS = ("sl_version", "sl_last_error", "sl_init", "sl_advect", "sl_advect_mul
            "sl_corrector_param_count", "sl_corrector_create", "sl_corrector_destroy", "sl_corrector_get_params",
            "sl_corrector_set_params", "sl_corrector_add_samples", "sl_corrector_get_rows", "sl_corrector_train",
            "sl_corrector_reset", "sl_advect_learned", "sl_selftest_wait_timeout", "sl_advect_wide_workspace",
-           "sl_advect_wide")
+           "sl_advect_wide", "sl_autotune_scheme", "sl_tuning_get", "sl_tuning_save", "sl_tuning_load",
+           "sl_tuning_clear", "sl_batch_autotune", "sl_batch_tuning")
+KERNELS = {1: "cec_fast", 2: "cec_split", 3: "cir_groups", 4: "unsplit"}
 
 
 class SLError(RuntimeError):
     def __init__(self, code, message):
         super().__init__(f"{STATUS.get(code, code)}: {message}")
         self.code = code
+
+
+class Tuning(ctypes.Structure):
+    """sl_tuning"""
+    _fields_ = [("kernel", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
+                ("tile_z", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {"kernel": KERNELS.get(self.kernel, self.kernel), "tile": [self.tile_x, self.tile_y],
+                "tile_z": self.tile_z, "ctas_per_sm": self.ctas_per_sm, "ms": float(self.ms)}
 
 
 class Instance(ctypes.Structure):
@@ -97,6 +109,13 @@ def load(path: str | None = None):
             "sl_selftest_wait_timeout": ([ctypes.c_uint, vp], i),
             "sl_advect_wide_workspace": ([i, i64p, i, i], ctypes.c_int64),
             "sl_advect_wide": ([vp, vp, vp, i, i64p, dp, d, i, i, i, vp, ctypes.c_int64, vp], i),
+            "sl_autotune_scheme": ([vp, vp, vp, i, i64p, dp, d, i, i, ctypes.POINTER(Tuning), vp], i),
+            "sl_tuning_get": ([i64p, i, i, ctypes.POINTER(Tuning)], i),
+            "sl_tuning_save": ([ctypes.c_char_p], i),
+            "sl_tuning_load": ([ctypes.c_char_p], i),
+            "sl_tuning_clear": ([], i),
+            "sl_batch_autotune": ([vp, ctypes.POINTER(Tuning), vp], i),
+            "sl_batch_tuning": ([vp, ctypes.POINTER(Tuning)], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -245,6 +264,47 @@ def sl_autotune(out, inp, vel, ndim, dims, spacing, dt, dtype, stream=None):
     _check(load().sl_autotune(_ptr(out), _ptr(inp), _ptr(vel), ndim, _i64(dims), _f64(spacing), float(dt),
                               int(dtype), ctypes.byref(tz), _stream(stream)))
     return tz.value
+
+
+def sl_autotune_scheme(out, inp, vel, ndim, dims, spacing, dt, scheme, dtype, stream=None):
+    t = Tuning()
+    _check(load().sl_autotune_scheme(_ptr(out), _ptr(inp), _ptr(vel), ndim, _i64(dims), _f64(spacing), float(dt),
+                                     int(scheme), int(dtype), ctypes.byref(t), _stream(stream)))
+    return t
+
+
+def sl_tuning_get(dims, scheme, dtype):
+    """The cached launch shape, or None when nothing is cached."""
+    t = Tuning()
+    rc = load().sl_tuning_get(_i64(dims), int(scheme), int(dtype), ctypes.byref(t))
+    if rc == -1:
+        return None
+    _check(rc)
+    return t
+
+
+def sl_tuning_save(path):
+    return _check(load().sl_tuning_save(os.fsencode(path)))
+
+
+def sl_tuning_load(path):
+    return _check(load().sl_tuning_load(os.fsencode(path)))
+
+
+def sl_tuning_clear():
+    return _check(load().sl_tuning_clear())
+
+
+def sl_batch_autotune(batch, stream=None):
+    t = Tuning()
+    _check(load().sl_batch_autotune(batch, ctypes.byref(t), _stream(stream)))
+    return t
+
+
+def sl_batch_tuning(batch):
+    t = Tuning()
+    _check(load().sl_batch_tuning(batch, ctypes.byref(t)))
+    return t
 
 
 def sl_corrector_param_count():

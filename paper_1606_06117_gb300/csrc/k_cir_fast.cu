@@ -28,16 +28,16 @@
 // consecutive rows issued by a quarter-warp fall on distinct banks.
 #include "sl_internal.h"
 
-// planes of Phi prefetched ahead, resident CTAs per SM the register budget is
-// compiled for, and the tile height (the tile is 32 cells wide)
+// planes of Phi prefetched ahead, and resident CTAs per SM the register budget
+// is compiled for (tile heights 16 and 32)
 #ifndef SL_CIR_PF
 #define SL_CIR_PF 2
 #endif
 #ifndef SL_CIR_MINB
 #define SL_CIR_MINB 4
 #endif
-#ifndef SL_CIR_TY
-#define SL_CIR_TY 16
+#ifndef SL_CIR_MINB32
+#define SL_CIR_MINB32 2
 #endif
 
 namespace sl {
@@ -374,8 +374,9 @@ cudaError_t go_cir(Geo g, int grid, const float *in, float *out, const float *ve
 bool cir_fast_eligible(int dtype, int ndim, const int64_t dims[3], bool aligned)
 {
     // FP32, 3D, 16-byte aligned rows of whole groups; Phi rows of a tile
-    // (columns [-4, 36)) and rows [-1, TY + 1) wrap at most once
-    return dtype == 0 && ndim == 3 && aligned && dims[0] % 4 == 0 && dims[0] >= 40 && dims[1] >= SL_CIR_TY &&
+    // (columns [-4, 36)) and rows [-1, TY + 1) wrap at most once (TY = 16, or
+    // 32 where dims[1] >= 32)
+    return dtype == 0 && ndim == 3 && aligned && dims[0] % 4 == 0 && dims[0] >= 40 && dims[1] >= 16 &&
            dims[0] * dims[1] < (int64_t(1) << 31);
 }
 
@@ -395,8 +396,12 @@ cudaError_t launch_cir_fast(const void *in, void *out, const void *vel, const in
     g.tz = lc.tz > 0 ? lc.tz : default_tz(0, 3, dims);
     if (g.tz > g.nz) g.tz = g.nz;
     g.chunks = (g.nz + g.tz - 1) / g.tz;
-    return go_cir<SL_CIR_TY, SL_CIR_PF, SL_CIR_MINB>(g, lc.grid, static_cast<const float *>(in),
-                                                     static_cast<float *>(out), static_cast<const float *>(vel), st);
+    const float *fi = static_cast<const float *>(in);
+    const float *fv = static_cast<const float *>(vel);
+    float *fo = static_cast<float *>(out);
+    // tile height 32 where a tile fits (a launch-shape choice), else 16
+    if (lc.ty == 32 && g.ny >= 32) return go_cir<32, SL_CIR_PF, SL_CIR_MINB32>(g, lc.grid, fi, fo, fv, st);
+    return go_cir<16, SL_CIR_PF, SL_CIR_MINB>(g, lc.grid, fi, fo, fv, st);
 }
 
 }  // namespace sl

@@ -389,7 +389,12 @@ cudaError_t launch_unsplit(int dtype, int scheme, const void *in, void *out, con
     const bool has_z = ndim == 3;
     if (dtype == 1) return by_shape<double, double, 8>(scheme, has_z, lc.aligned && g.nx % 2 == 0, g, lc.grid, in, out, vel, st);
     if (dtype == 2) return by_shape<float, double, 16>(scheme, has_z, lc.aligned && g.nx % 4 == 0, g, lc.grid, in, out, vel, st);
-    return by_shape<float, float, 16>(scheme, has_z, lc.aligned && g.nx % 4 == 0, g, lc.grid, in, out, vel, st);
+    const bool vec = lc.aligned && g.nx % 4 == 0;
+    // FP32 3D grids with vector staging: tile heights 8 and 32 besides 16 (a
+    // launch-shape choice; a cell's arithmetic does not depend on it)
+    if (has_z && vec && lc.ty == 8) return by_scheme<float, float, 8, true, true>(scheme, g, lc.grid, in, out, vel, st);
+    if (has_z && vec && lc.ty == 32) return by_scheme<float, float, 32, true, true>(scheme, g, lc.grid, in, out, vel, st);
+    return by_shape<float, float, 16>(scheme, has_z, vec, g, lc.grid, in, out, vel, st);
 }
 
 }  // namespace sl

@@ -77,13 +77,18 @@ bool pipe_ready(HostPipe &p)
     return true;
 }
 
-// autotuned launch shape per (nx, ny, nz, dtype): z chunk of the generic
-// kernels and CTA count of the fast persistent CEC kernel
-struct Tuned {
-    int tz = 0;
-    int grid = 0;
-};
-std::map<std::tuple<int64_t, int64_t, int64_t, int>, Tuned> g_tuned;
+// autotuned launch shapes per (nx, ny, nz, scheme, dtype)
+using TuneKey = std::tuple<int64_t, int64_t, int64_t, int, int>;
+std::map<TuneKey, sl_tuning> g_tuned;
+
+bool tuned_get(const int64_t dims[3], int scheme, int dtype, sl_tuning &t)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_tuned.find(TuneKey(dims[0], dims[1], dims[2], scheme, dtype));
+    if (it == g_tuned.end()) return false;
+    t = it->second;
+    return true;
+}
 
 int fail(int code, const char *fmt, ...)
 {
@@ -134,28 +139,61 @@ int check_geometry(int ndim, const int64_t dims[3], const double spacing[3], dou
 
 int64_t ncell_of(const int64_t dims[3]) { return dims[0] * dims[1] * dims[2]; }
 
+// The kernel family that serves a request (fixed by the request; the tuner
+// only chooses among launch shapes of that family).
+int family_of(int scheme, int dtype, int ndim, const int64_t dims[3], bool aligned)
+{
+    if (scheme == SL_CEC) return fast_eligible(dims, ndim, dtype, aligned) ? SL_KERNEL_CEC_FAST : SL_KERNEL_CEC_SPLIT;
+    if (scheme == SL_CIR && cir_fast_eligible(dtype, ndim, dims, aligned)) return SL_KERNEL_CIR_GROUPS;
+    return SL_KERNEL_UNSPLIT;
+}
+
+// Tile height of a family's launch with no height chosen (the kernels' defaults).
+int default_ty(int fam, int dtype)
+{
+    switch (fam) {
+    case SL_KERNEL_CEC_FAST: return 32;
+    case SL_KERNEL_CEC_SPLIT: return dtype == SL_F64 ? 16 : 32;
+    case SL_KERNEL_CIR_GROUPS: return 16;
+    default: return dtype == SL_F64 ? 8 : 16;
+    }
+}
+
+// The launch shape of a request: the cached choice when it was tuned on the
+// family that serves the request, else the family's defaults.
+Launch launch_for(int fam, const int64_t dims[3], int scheme, int dtype, bool aligned, const DevCtx *c)
+{
+    Launch lc;
+    lc.aligned = aligned;
+    sl_tuning t;
+    if (tuned_get(dims, scheme, dtype, t) && t.kernel == fam) {
+        lc.tz = t.tile_z;
+        lc.ty = t.tile_y;
+        lc.grid = t.ctas_per_sm > 0 ? t.ctas_per_sm * c->num_sms : 0;
+    }
+    return lc;
+}
+
+cudaError_t launch_family(int fam, const Launch &lc, void *out, const void *in, const void *vel, int ndim,
+                          const int64_t dims[3], const double s[3], int scheme, int dtype, int parity,
+                          cudaStream_t st, DevCtx *c)
+{
+    if (fam == SL_KERNEL_CEC_FAST) {
+        FastInst one;
+        fast_fill(one, in, out, vel, dims, s, 0);
+        return launch_cec_fast(one, nullptr, 1, (int64_t)one.ntiles * one.nz, parity, c->status, lc.grid, st);
+    }
+    if (fam == SL_KERNEL_CEC_SPLIT) return launch_split_cec(dtype, in, out, vel, ndim, dims, s, parity, lc, c->status, st);
+    return launch_unsplit(dtype, scheme, in, out, vel, ndim, dims, s, lc, c->status, st);
+}
+
 int launch_step(void *out, const void *in, const void *vel, int ndim, const int64_t dims[3], const double s[3],
                 int scheme, int dtype, int parity, cudaStream_t st, DevCtx *c)
 {
-    Launch lc;
-    lc.aligned = aligned16(out) && aligned16(in) && aligned16(vel);
-    Tuned tu;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        auto it = g_tuned.find(std::make_tuple(dims[0], dims[1], dims[2], dtype));
-        if (it != g_tuned.end()) tu = it->second;
-    }
-    cudaError_t e;
-    if (scheme == SL_CEC && fast_eligible(dims, ndim, dtype, lc.aligned)) {
-        FastInst one;
-        fast_fill(one, in, out, vel, dims, s, 0);
-        e = launch_cec_fast(one, nullptr, 1, (int64_t)one.ntiles * one.nz, parity, c->status, tu.grid, st);
-    } else if (scheme == SL_CEC) {
-        lc.tz = tu.tz;
-        e = launch_split_cec(dtype, in, out, vel, ndim, dims, s, parity, lc, c->status, st);
-    } else {
-        e = launch_unsplit(dtype, scheme, in, out, vel, ndim, dims, s, lc, c->status, st);
-    }
+    const bool aligned = aligned16(out) && aligned16(in) && aligned16(vel);
+    const int fam = family_of(scheme, dtype, ndim, dims, aligned);
+    const Launch lc = launch_for(fam, dims, scheme, dtype, aligned, c);
+    const cudaError_t e = launch_family(fam, lc, out, in, vel, ndim, dims, s, scheme, dtype, parity, st, c);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return SL_OK;
 }
@@ -202,6 +240,8 @@ struct sl_batch {
     unsigned *counter = nullptr;   // owns the device allocation
     int nitems[2] = {0, 0};
     int grid[2] = {0, 0};
+    int fast_grid = 0;             // fast path: CTAs (0 = the kernel's default)
+    sl_tuning tuning{};            // current launch shape, as reported
 };
 
 extern "C" {
@@ -260,12 +300,7 @@ int sl_advect_multi(void *const *outs, const void *const *ins, int nfields, cons
     if (scheme == SL_CEC && fast_eligible(dims, ndim, dtype, aligned)) {
         // groups of up to kFastFields fields per launch: the CTAs of a group
         // share one velocity read through L2
-        Tuned tu;
-        {
-            std::lock_guard<std::mutex> lk(g_mu);
-            auto it = g_tuned.find(std::make_tuple(dims[0], dims[1], dims[2], dtype));
-            if (it != g_tuned.end()) tu = it->second;
-        }
+        const Launch lc = launch_for(SL_KERNEL_CEC_FAST, dims, scheme, dtype, aligned, c);
         for (int f0 = 0; f0 < nfields; f0 += kFastFields) {
             const int nf = std::min(kFastFields, nfields - f0);
             FastInst one;
@@ -276,7 +311,7 @@ int sl_advect_multi(void *const *outs, const void *const *ins, int nfields, cons
                 one.fout[i] = static_cast<float *>(outs[f0 + i]);
             }
             const cudaError_t e = launch_cec_fast(one, nullptr, 1, (int64_t)one.ntiles * one.nz, step_parity,
-                                                  c->status, tu.grid, st);
+                                                  c->status, lc.grid, st);
             if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         }
         return SL_OK;
@@ -358,6 +393,7 @@ int sl_advect_host(void *out, const void *in, const void *vel, int ndim, const i
             e = cudaMemcpyAsync(d_vel + d * fb + off, h_vel + d * fb + off, n, cudaMemcpyHostToDevice, pp.in);
         return e;
     };
+    const Launch lc_fast = launch_for(SL_KERNEL_CEC_FAST, dims, scheme, dtype, true, c);
     cudaError_t e = cudaEventRecord(pp.start, st);
     for (cudaStream_t q : {pp.in, pp.run, pp.back})
         if (e == cudaSuccess) e = cudaStreamWaitEvent(q, pp.start, 0);
@@ -377,7 +413,7 @@ int sl_advect_host(void *out, const void *in, const void *vel, int ndim, const i
         fast_fill(one, d_in, d_out, d_vel, dims, s, 0);
         one.zb = (int)a;
         one.nzr = (int)(b - a);
-        e = launch_cec_fast(one, nullptr, 1, (int64_t)one.ntiles * one.nzr, step_parity, c->status, 0, pp.run);
+        e = launch_cec_fast(one, nullptr, 1, (int64_t)one.ntiles * one.nzr, step_parity, c->status, lc_fast.grid, pp.run);
         if (e != cudaSuccess) {
             what = "kernel launch";
             break;
@@ -486,6 +522,12 @@ int sl_batch_create(sl_batch **out, const sl_instance *inst, int n, int scheme, 
         const size_t fb = (size_t)ncell_of(in.dims) * 4;
         if (overlap(in.a, fb, in.b, fb) || overlap(in.b, fb, in.vel, 3 * fb) || overlap(in.a, fb, in.vel, 3 * fb))
             return fail(SL_ERR_ALIAS, "instance %d: buffers overlap", i);
+        // planes per work item: the argument, else the choice cached for the
+        // generic split kernel on this grid, else 32
+        int tz_cached = 32;
+        sl_tuning tc;
+        if (tuned_get(in.dims, SL_CEC, dtype, tc) && tc.kernel == SL_KERNEL_CEC_SPLIT && tc.tile_z > 0)
+            tz_cached = tc.tile_z;
         BatchRec &r = recs[i];
         r.a = in.a;
         r.b = in.b;
@@ -503,7 +545,7 @@ int sl_batch_create(sl_batch **out, const sl_instance *inst, int n, int scheme, 
             g.sy = s[1];
             g.sz = s[2];
             g.status = c->status;
-            g.tz = tile_z > 0 ? std::min(tile_z, g.nz) : std::min(32, g.nz);
+            g.tz = tile_z > 0 ? std::min(tile_z, g.nz) : std::min(tz_cached, g.nz);
             g.chunks = (g.nz + g.tz - 1) / g.tz;
             g.tiles_x = (g.nx + tx - 1) / tx;
             g.tiles_y = (g.ny + ty - 1) / ty;
@@ -533,6 +575,12 @@ int sl_batch_create(sl_batch **out, const sl_instance *inst, int n, int scheme, 
     b->nitems[0] = total[0];
     b->nitems[1] = total[1];
     for (int par = 0; par < 2; ++par) b->grid[par] = std::min(total[par], c->num_sms * batched_blocks_per_sm(par));
+    b->tuning.kernel = fast ? SL_KERNEL_CEC_FAST : SL_KERNEL_CEC_SPLIT;
+    b->tuning.tile_x = 32;
+    b->tuning.tile_y = 32;
+    b->tuning.tile_z = fast ? 0 : recs[0].g[0].tz;
+    b->tuning.ctas_per_sm = fast ? std::max(1, fast_grid(0) / c->num_sms) : batched_blocks_per_sm(0);
+    b->tuning.ms = 0.f;
     void *p = nullptr;
     const size_t rec_bytes = (sizeof(BatchRec) * n + 255) & ~(size_t)255;
     const size_t fast_bytes = (sizeof(FastInst) * 2 * n + 255) & ~(size_t)255;
@@ -579,13 +627,81 @@ int sl_batch_step(sl_batch *b, int step_index, void *stream)
     cudaError_t e;
     if (b->fast) {
         FastInst dummy{};
-        e = launch_cec_fast(dummy, b->dev_fast + (size_t)par * b->n, b->n, b->fast_total, par, c->status, 0, st);
+        e = launch_cec_fast(dummy, b->dev_fast + (size_t)par * b->n, b->n, b->fast_total, par, c->status, b->fast_grid, st);
     } else {
         e = cudaMemsetAsync(b->counter, 0, sizeof(unsigned), st);
         if (e == cudaSuccess)
             e = launch_batched_cec(b->dev_recs, b->n, b->nitems[par], par, b->counter, c->status, b->grid[par], st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+    return SL_OK;
+}
+
+int sl_batch_autotune(sl_batch *b, sl_tuning *best, void *stream)
+{
+    if (!b) return fail(SL_ERR_ARG, "batch is NULL");
+    DevCtx *c = ctx_get();
+    if (!c) return fail(SL_ERR_CUDA, "could not create the device context");
+    if (c->device != b->device) return fail(SL_ERR_ARG, "batch belongs to device %d", b->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // candidate CTAs per SM within the kernel's occupancy (even steps only: A -> B)
+    const int occ = b->fast ? std::max(1, fast_grid(0) / c->num_sms) : batched_blocks_per_sm(0);
+    std::vector<int> cands;
+    for (int k : {1, 2, 4})
+        if (k <= occ) cands.push_back(k);
+    const int saved_fast = b->fast_grid, saved0 = b->grid[0], saved1 = b->grid[1];
+    auto set = [&](int k) {
+        if (b->fast) {
+            b->fast_grid = k * c->num_sms;
+        } else {
+            b->grid[0] = std::min(b->nitems[0], k * c->num_sms);
+            b->grid[1] = std::min(b->nitems[1], std::min(k, batched_blocks_per_sm(1)) * c->num_sms);
+        }
+    };
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return fail(SL_ERR_CUDA, "events");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(SL_ERR_CUDA, "events");
+    }
+    float best_ms = 1e30f;
+    int best_k = cands.front();
+    int rc = SL_OK;
+    for (int k : cands) {
+        set(k);
+        rc = sl_batch_step(b, 0, stream);   // warm-up
+        float ms = 0.f;
+        cudaError_t e = rc ? cudaSuccess : cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && !rc && e == cudaSuccess; ++r) rc = sl_batch_step(b, 0, stream);
+        if (!rc && e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (!rc && e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (!rc && e != cudaSuccess) rc = cuda_fail(e, "batch autotune");
+        if (rc) break;
+        if (ms / 3.f < best_ms) {
+            best_ms = ms / 3.f;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        b->fast_grid = saved_fast;
+        b->grid[0] = saved0;
+        b->grid[1] = saved1;
+        return rc;
+    }
+    set(best_k);
+    b->tuning.ctas_per_sm = best_k;
+    b->tuning.ms = best_ms;
+    if (best) *best = b->tuning;
+    return SL_OK;
+}
+
+int sl_batch_tuning(const sl_batch *b, sl_tuning *out)
+{
+    if (!b || !out) return fail(SL_ERR_ARG, "batch and out must not be NULL");
+    *out = b->tuning;
     return SL_OK;
 }
 
@@ -635,10 +751,11 @@ int sl_advect_wide(void *out, const void *in, const void *vel, int ndim, const i
     return SL_OK;
 }
 
-int sl_autotune(void *out, const void *in, const void *vel, int ndim, const int64_t dims[3], const double spacing[3],
-                double dt, int dtype, int *tile_z, void *stream)
+int sl_autotune_scheme(void *out, const void *in, const void *vel, int ndim, const int64_t dims[3],
+                       const double spacing[3], double dt, int scheme, int dtype, sl_tuning *best, void *stream)
 {
-    if (!out || !in || !vel || !tile_z) return fail(SL_ERR_ARG, "NULL argument");
+    if (!out || !in || !vel) return fail(SL_ERR_ARG, "out, in and vel must not be NULL");
+    if (scheme < SL_CIR || scheme > SL_CEC) return fail(SL_ERR_ARG, "unknown scheme %d", scheme);
     double s[3];
     int rc = check_geometry(ndim, dims, spacing, dt, dtype, s);
     if (rc) return rc;
@@ -647,65 +764,190 @@ int sl_autotune(void *out, const void *in, const void *vel, int ndim, const int6
     DevCtx *c = ctx_get();
     if (!c) return fail(SL_ERR_CUDA, "could not create the device context");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (ndim == 2) {
-        *tile_z = 1;
-        return SL_OK;
-    }
-    const bool fast = fast_eligible(dims, ndim, dtype, aligned16(out) && aligned16(in) && aligned16(vel));
-    std::vector<int> cands;
-    if (fast) {
-        // CTA counts of the persistent kernel: whole waves of 1 or 2 CTAs per SM
-        const int g1 = fast_grid(0) / 2 > 0 ? fast_grid(0) / 2 : c->num_sms;
-        for (int g : {g1, 2 * g1}) cands.push_back(g);
-    } else {
-        for (int tz : {8, 16, 24, 32, 48, 64, 96, 128, 192, 256})
-            if (tz <= dims[2]) cands.push_back(tz);
-        if (cands.empty() || cands.back() != (int)dims[2]) cands.push_back((int)dims[2]);
-    }
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(SL_ERR_CUDA, "events");
-    float best = 1e30f;
-    int best_tz = cands.front();
-    Launch lc;
-    lc.aligned = aligned16(out) && aligned16(in) && aligned16(vel);
-    FastInst one;
-    fast_fill(one, in, out, vel, dims, s, 0);
-    auto run = [&](int cand, int rep) {
-        if (fast) return launch_cec_fast(one, nullptr, 1, (int64_t)one.ntiles * one.nz, rep, c->status, cand, st);
-        lc.tz = cand;
-        return launch_split_cec(dtype, in, out, vel, ndim, dims, s, rep, lc, c->status, st);
+    const bool aligned = aligned16(out) && aligned16(in) && aligned16(vel);
+    const int fam = family_of(scheme, dtype, ndim, dims, aligned);
+
+    // candidates: (tile height, planes per item, CTAs per SM); 0 = the default
+    struct Cand {
+        int ty, tz, ctas;
     };
-    for (int cand : cands) {
-        float tot = 0.0f;
-        cudaError_t e = cudaSuccess;
-        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
-            e = run(cand, rep);   // warm-up
-            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-            if (e == cudaSuccess) e = run(cand, rep);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.0f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            tot += ms;
+    std::vector<Cand> cands;
+    std::vector<int> tzs;
+    if (ndim == 3) {
+        for (int tz : {8, 16, 32, 64, 128, 256})
+            if (tz < dims[2]) tzs.push_back(tz);
+        tzs.push_back((int)dims[2]);
+    } else {
+        tzs.push_back(1);
+    }
+    if (fam == SL_KERNEL_CEC_FAST) {
+        const int occ = std::max(1, fast_grid(0) / c->num_sms);
+        for (int k = 1; k <= std::min(occ, 2); ++k) cands.push_back({0, 0, k});
+    } else if (fam == SL_KERNEL_CEC_SPLIT) {
+        for (int tz : tzs) cands.push_back({0, tz, 0});
+    } else if (fam == SL_KERNEL_CIR_GROUPS) {
+        for (int ty : {16, 32})
+            if (ty == 16 || dims[1] >= 32)
+                for (int tz : tzs) cands.push_back({ty, tz, 0});
+    } else {
+        std::vector<int> tys = {0};
+        if (dtype == SL_F32 && ndim == 3 && aligned && dims[0] % 4 == 0) tys = {8, 16, 32};
+        for (int ty : tys) {
+            if (scheme == SL_BEC && ndim == 3)
+                for (int k = 1; k <= 3; ++k) cands.push_back({ty, 0, k});
+            else
+                for (int tz : tzs) cands.push_back({ty, tz, 0});
         }
-        if (e != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return cuda_fail(e, "autotune");
-        }
-        if (tot < best) {
-            best = tot;
-            best_tz = cand;
+    }
+
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return fail(SL_ERR_CUDA, "events");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(SL_ERR_CUDA, "events");
+    }
+    const int reps = scheme == SL_CEC ? 4 : 3;   // both sweep orders for SL_CEC
+    float best_ms = 1e30f;
+    Cand pick = cands.front();
+    cudaError_t e = cudaSuccess;
+    for (const Cand &cd : cands) {
+        Launch lc;
+        lc.aligned = aligned;
+        lc.ty = cd.ty;
+        lc.tz = cd.tz;
+        lc.grid = cd.ctas > 0 ? cd.ctas * c->num_sms : 0;
+        e = launch_family(fam, lc, out, in, vel, ndim, dims, s, scheme, dtype, 0, st, c);   // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r)
+            e = launch_family(fam, lc, out, in, vel, ndim, dims, s, scheme, dtype, r & 1, st, c);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) break;
+        if (ms / reps < best_ms) {
+            best_ms = ms / reps;
+            pick = cd;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    sl_tuning t;
+    t.kernel = fam;
+    t.tile_x = 32;
+    t.tile_y = pick.ty > 0 ? pick.ty : default_ty(fam, dtype);
+    if (fam == SL_KERNEL_CIR_GROUPS && t.tile_y == 32 && dims[1] < 32) t.tile_y = 16;
+    t.tile_z = pick.tz;
+    t.ctas_per_sm = pick.ctas;
+    t.ms = best_ms;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        Tuned &t = g_tuned[std::make_tuple(dims[0], dims[1], dims[2], dtype)];
-        if (fast) t.grid = best_tz; else t.tz = best_tz;
+        g_tuned[TuneKey(dims[0], dims[1], dims[2], scheme, dtype)] = t;
     }
-    *tile_z = best_tz;
+    if (best) *best = t;
+    return SL_OK;
+}
+
+int sl_autotune(void *out, const void *in, const void *vel, int ndim, const int64_t dims[3], const double spacing[3],
+                double dt, int dtype, int *tile_z, void *stream)
+{
+    if (!tile_z) return fail(SL_ERR_ARG, "NULL argument");
+    sl_tuning t;
+    const int rc = sl_autotune_scheme(out, in, vel, ndim, dims, spacing, dt, SL_CEC, dtype, &t, stream);
+    if (rc) return rc;
+    if (t.kernel == SL_KERNEL_CEC_FAST) {
+        DevCtx *c = ctx_get();
+        *tile_z = t.ctas_per_sm * (c ? c->num_sms : 1);
+    } else {
+        *tile_z = t.tile_z;
+    }
+    return SL_OK;
+}
+
+int sl_tuning_get(const int64_t dims[3], int scheme, int dtype, sl_tuning *out)
+{
+    if (!dims || !out) return fail(SL_ERR_ARG, "dims and out must not be NULL");
+    if (!tuned_get(dims, scheme, dtype, *out)) return fail(SL_ERR_ARG, "no launch shape cached for this grid");
+    return SL_OK;
+}
+
+int sl_tuning_clear(void)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tuned.clear();
+    return SL_OK;
+}
+
+int sl_tuning_save(const char *path)
+{
+    if (!path) return fail(SL_ERR_ARG, "path is NULL");
+    std::vector<std::pair<TuneKey, sl_tuning>> all;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        all.assign(g_tuned.begin(), g_tuned.end());
+    }
+    FILE *f = std::fopen(path, "w");
+    if (!f) return fail(SL_ERR_ARG, "cannot write %s", path);
+    char name[256] = "unknown";
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
+        std::snprintf(name, sizeof name, "%s", prop.name);
+    else
+        cudaGetLastError();   // no device: clear the error and write the entries anyway
+    std::fprintf(f, "# libsl launch shapes, timed on %s: nx ny nz scheme dtype kernel tile_x tile_y tile_z ctas_per_sm ms\n", name);
+    for (const auto &kv : all) {
+        const sl_tuning &t = kv.second;
+        std::fprintf(f, "%lld %lld %lld %d %d %d %d %d %d %d %.6g\n", (long long)std::get<0>(kv.first),
+                     (long long)std::get<1>(kv.first), (long long)std::get<2>(kv.first), std::get<3>(kv.first),
+                     std::get<4>(kv.first), t.kernel, t.tile_x, t.tile_y, t.tile_z, t.ctas_per_sm, (double)t.ms);
+    }
+    const bool ok = std::ferror(f) == 0;
+    if (std::fclose(f) != 0 || !ok) return fail(SL_ERR_ARG, "write error on %s", path);
+    return SL_OK;
+}
+
+int sl_tuning_load(const char *path)
+{
+    if (!path) return fail(SL_ERR_ARG, "path is NULL");
+    FILE *f = std::fopen(path, "r");
+    if (!f) return fail(SL_ERR_ARG, "cannot read %s", path);
+    std::vector<std::pair<TuneKey, sl_tuning>> got;
+    char line[512];
+    int lineno = 0;
+    while (std::fgets(line, sizeof line, f)) {
+        ++lineno;
+        const char *q = line;
+        while (*q == ' ' || *q == '\t') ++q;
+        if (*q == '#' || *q == '\n' || *q == '\0') continue;
+        long long nx, ny, nz;
+        int scheme, dtype, kernel, tx, ty, tz, ctas;
+        double ms;
+        char extra;
+        const int n = std::sscanf(q, "%lld %lld %lld %d %d %d %d %d %d %d %lf %c", &nx, &ny, &nz, &scheme, &dtype,
+                                  &kernel, &tx, &ty, &tz, &ctas, &ms, &extra);
+        const bool ok = n == 11 && nx >= 1 && ny >= 1 && nz >= 1 && nx <= (1ll << 30) && ny <= (1ll << 30) &&
+                        nz <= (1ll << 30) && scheme >= SL_CIR && scheme <= SL_CEC && dtype >= SL_F32 &&
+                        dtype <= SL_F32_D64 && kernel >= SL_KERNEL_CEC_FAST && kernel <= SL_KERNEL_UNSPLIT &&
+                        tx == 32 && (ty == 8 || ty == 16 || ty == 32) && tz >= 0 && tz <= (1 << 30) && ctas >= 0 &&
+                        ctas <= 32 && std::isfinite(ms);
+        if (!ok) {
+            std::fclose(f);
+            return fail(SL_ERR_ARG, "%s line %d: malformed launch shape", path, lineno);
+        }
+        sl_tuning t;
+        t.kernel = kernel;
+        t.tile_x = tx;
+        t.tile_y = ty;
+        t.tile_z = tz;
+        t.ctas_per_sm = ctas;
+        t.ms = (float)ms;
+        got.emplace_back(TuneKey(nx, ny, nz, scheme, dtype), t);
+    }
+    std::fclose(f);
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (const auto &kv : got) g_tuned[kv.first] = kv.second;
     return SL_OK;
 }
 

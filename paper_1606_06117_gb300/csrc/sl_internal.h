@@ -25,7 +25,8 @@ DevCtx *ctx_get();   // context of the current device, created on demand
 // Launch configuration chosen for a fused kernel.
 struct Launch {
     int tz = 0;          // z chunk (planes per work item); 0 = default
-    int grid = 0;        // CTAs; 0 = one per item
+    int ty = 0;          // column tile height among a kernel's compiled variants; 0 = default
+    int grid = 0;        // CTAs; 0 = one per item (persistent kernels: their occupancy)
     bool aligned = true; // all base pointers 16-byte aligned (vector staging allowed)
 };
 
