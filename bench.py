@@ -53,6 +53,8 @@ def parse():
                     help="only warm-up and timed learned-corrector steps (untrained weights; for ncu)")
     ap.add_argument("--scheme", choices=["CIR", "FEC", "BEC", "CEC"], default="CEC",
                     help="scheme of the --profile steps")
+    ap.add_argument("--jsonl", default=None,
+                    help="also append one JSON record per measurement of the line to this file")
     return ap.parse_args()
 
 
@@ -286,6 +288,65 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ metrics records
+def jsonl_records(line, when=None):
+    """Flatten a bench line into one record per measurement: throughput
+    (Gcell/s and GB/s of algorithmic bytes), roofline fraction, errors against
+    the oracle or the exact solution, and the host cores of the CPU baseline."""
+    when = when or time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())
+    base = {"time": when, "n_gpus": line.get("n_gpus"), "clocks": line.get("clocks")}
+    recs = []
+    roof = line.get("roofline") or {}
+    recs.append(dict(base, record="headline", workload=line["config"]["workload"], gcell_s=line["value"],
+                     ms_per_step=line["ms_per_step"], gb_s=roof.get("achieved"), roofline_frac=roof.get("frac"),
+                     traffic_bytes=roof.get("traffic"), launch=line["config"].get("launch")))
+    if line.get("e2e"):
+        recs.append(dict(base, record="e2e", gcell_s=line["e2e"]["value"],
+                         h2d_bytes_per_step=line["e2e"]["h2d_bytes_per_step"],
+                         d2h_bytes_per_step=line["e2e"]["d2h_bytes_per_step"]))
+    if line.get("cpu_baseline"):
+        cb = line["cpu_baseline"]
+        recs.append(dict(base, record="cpu_baseline", gcell_s=cb["value"], host_cores=cb["cores"], sample=cb["sample"]))
+    for name, r in (line.get("schemes") or {}).items():
+        gb = BYTES_PER_CELL * r["gcell_s"]   # GB/s of algorithmic bytes
+        peak = roof.get("peak")
+        recs.append(dict(base, record="scheme", scheme=name, gcell_s=r["gcell_s"], ms_per_step=r["ms_per_step"],
+                         gb_s=gb, roofline_frac=gb / peak if peak else None,
+                         roundtrip_rel_l2=r.get("roundtrip_rel_l2_100_100"), launch=r.get("launch")))
+    if line.get("cec_256"):
+        c = line["cec_256"]
+        recs.append(dict(base, record="cec_256", gcell_s=c["gcell_s"], ms_per_step=c["ms_per_step"],
+                         gb_s=c["roofline"]["achieved"], roofline_frac=c["roofline"]["frac"]))
+    if line.get("batched_c3"):
+        b = line["batched_c3"]
+        recs.append(dict(base, record="batched_c3", gcell_s=b["batched_graph"]["gcell_s"],
+                         plain_gcell_s=b["plain_48_launches"]["gcell_s"], launch=b.get("launch")))
+    if line.get("deformation_c5"):
+        d = line["deformation_c5"]
+        recs.append(dict(base, record="deformation_c5", field_gcell_s=d["field_gcell_s"],
+                         rel_l2_vs_exact=d.get("rel_l2_at_T")))
+    if line.get("learned_c4"):
+        lc = line["learned_c4"]
+        recs.append(dict(base, record="learned_c4", gcell_s=lc["learned_gcell_s"],
+                         roofline_frac=lc["roofline"]["frac"], fell_back_at_step=lc.get("fell_back_at_step"),
+                         checks=lc.get("checks")))
+    if line.get("rotation_c1"):
+        r = line["rotation_c1"]
+        recs.append(dict(base, record="rotation_c1", **{k: {"rel_l2_vs_exact": v["rel_l2"], "linf_vs_exact": v["linf"]}
+                                                         for k, v in r.items() if isinstance(v, dict)}))
+    if line.get("large_cfl_f2"):
+        w = line["large_cfl_f2"]
+        recs.append(dict(base, record="large_cfl_f2", gcell_s=w["gcell_s"], roofline_frac=w["roofline"]["frac"],
+                         roundtrip_rel_l2=w["roundtrip_rel_l2"]))
+    return recs
+
+
+def write_jsonl(path, line):
+    with open(path, "a") as fh:
+        for rec in jsonl_records(line):
+            fh.write(json.dumps(rec) + "\n")
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import torch
@@ -453,6 +514,8 @@ def run_ours(args):
                 "device_status": sl_status}
         line.update(extras)
         print(json.dumps(line), flush=True)
+        if args.jsonl:
+            write_jsonl(args.jsonl, line)
     if world > 1:
         dist.destroy_process_group()
 

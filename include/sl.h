@@ -206,6 +206,25 @@ int sl_selftest_wait_timeout(unsigned polls, void *stream);
 int sl_device_status(void *stream, unsigned *out_bits);
 
 /*
+ * Checkpoints of a field for long runs (no counterpart in the paper).
+ * sl_field_save copies the device field (prod(dims) elements of dtype's
+ * storage type: float for SL_F32 and SL_F32_D64, double for SL_F64) to the
+ * file at path: one JSON header line (format, version, ndim, dims, dtype,
+ * step, payload bytes, FNV-1a 64 checksum of the payload) followed by the raw
+ * little-endian payload.  sl_field_load checks that the file holds exactly
+ * that grid and type, that the payload is complete and its checksum matches,
+ * then copies it into the device field and returns the saved step in *step
+ * (may be NULL).  Both synchronise the stream and return when done.
+ * Errors: SL_ERR_ARG (NULL argument, bad geometry, unreadable / unwritable
+ * file, another grid or type, a truncated or corrupted payload: the device
+ * field is not touched then), SL_ERR_NOMEM (host buffer), SL_ERR_CUDA.
+ */
+int sl_field_save(const char *path, const void *field, int ndim, const int64_t dims[3],
+                  int dtype, int64_t step, void *stream);
+int sl_field_load(const char *path, void *field, int ndim, const int64_t dims[3],
+                  int dtype, int64_t *step, void *stream);
+
+/*
  * Autotuning of launch shapes (no counterpart in the paper).
  *
  * The kernel that serves a step is fixed by the request (scheme, dtype,
@@ -416,6 +435,17 @@ int sl_corrector_train(sl_corrector *c, int iters, int batch, float lr, uint64_t
                        float *last_loss, void *stream);
 /* Clear the fallback flag (learned steps resume). */
 int sl_corrector_reset(sl_corrector *c);
+/*
+ * Save the network's parameters to the file at path, or load them from one
+ * written by sl_corrector_save (a JSON header line, then the 8577 FP32 values
+ * and their FNV-1a checksum, as sl_field_save).  Loading replaces the
+ * parameters as sl_corrector_set_params does (and clears the fallback state).
+ * Errors: SL_ERR_ARG (NULL argument, unreadable / unwritable file, a file of
+ * another kind or network, a short payload, trailing bytes or a checksum
+ * mismatch: nothing is loaded then), SL_ERR_CUDA.  Synchronous.
+ */
+int sl_corrector_save(sl_corrector *c, const char *path);
+int sl_corrector_load(sl_corrector *c, const char *path);
 /*
  * One step with the corrector: FP32 fields, ndim = 3, dims[0] % 32 == 0,
  * dims[1] % 4 == 0, dims[2] >= 3, in 16-byte aligned (else SL_ERR_UNSUPPORTED).

@@ -34,7 +34,8 @@ EXPORTS = ("sl_version", "sl_last_error", "sl_init", "sl_advect", "sl_advect_mul
            "sl_corrector_set_params", "sl_corrector_add_samples", "sl_corrector_get_rows", "sl_corrector_train",
            "sl_corrector_reset", "sl_advect_learned", "sl_selftest_wait_timeout", "sl_advect_wide_workspace",
            "sl_advect_wide", "sl_autotune_scheme", "sl_tuning_get", "sl_tuning_save", "sl_tuning_load",
-           "sl_tuning_clear", "sl_batch_autotune", "sl_batch_tuning")
+           "sl_tuning_clear", "sl_batch_autotune", "sl_batch_tuning", "sl_field_save", "sl_field_load",
+           "sl_corrector_save", "sl_corrector_load")
 KERNELS = {1: "cec_fast", 2: "cec_split", 3: "cir_groups", 4: "unsplit"}
 
 
@@ -116,6 +117,10 @@ def load(path: str | None = None):
             "sl_tuning_clear": ([], i),
             "sl_batch_autotune": ([vp, ctypes.POINTER(Tuning), vp], i),
             "sl_batch_tuning": ([vp, ctypes.POINTER(Tuning)], i),
+            "sl_field_save": ([ctypes.c_char_p, vp, i, i64p, i, ctypes.c_int64, vp], i),
+            "sl_field_load": ([ctypes.c_char_p, vp, i, i64p, i, ctypes.POINTER(ctypes.c_int64), vp], i),
+            "sl_corrector_save": ([vp, ctypes.c_char_p], i),
+            "sl_corrector_load": ([vp, ctypes.c_char_p], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -305,6 +310,27 @@ def sl_batch_tuning(batch):
     t = Tuning()
     _check(load().sl_batch_tuning(batch, ctypes.byref(t)))
     return t
+
+
+def sl_field_save(path, field, ndim, dims, dtype, step=0, stream=None):
+    return _check(load().sl_field_save(os.fsencode(path), _ptr(field), int(ndim), _i64(dims), int(dtype),
+                                       int(step), _stream(stream)))
+
+
+def sl_field_load(path, field, ndim, dims, dtype, stream=None):
+    """Returns the saved step."""
+    step = ctypes.c_int64()
+    _check(load().sl_field_load(os.fsencode(path), _ptr(field), int(ndim), _i64(dims), int(dtype),
+                                ctypes.byref(step), _stream(stream)))
+    return step.value
+
+
+def sl_corrector_save(c, path):
+    return _check(load().sl_corrector_save(c, os.fsencode(path)))
+
+
+def sl_corrector_load(c, path):
+    return _check(load().sl_corrector_load(c, os.fsencode(path)))
 
 
 def sl_corrector_param_count():
