@@ -240,6 +240,21 @@ class OracleReplicas:
             self.pool.shutdown()
 
 
+def rb_oracle_rate(n, Ra, dt, nsteps=200):
+    """Time per step of the FP64 oracle's Rayleigh-Benard box (one thread of
+    numpy; the dense pseudo-inverse is built before the timed steps)."""
+    from oracle import rb_oracle as R
+    from paper_1606_06117_gb300 import workloads as W
+    box = R.Box(n, n, Ra=Ra, scheme="CEC")
+    box.theta = W.rb_spots(n, n)
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        box.step(dt)
+    el = time.perf_counter() - t0
+    return {"value": el / nsteps * 1e6, "unit": "us/step", "cores": 1, "kind": "oracle",
+            "sample": f"{nsteps} CEC steps of the {n}x{n} box ({el:.1f} s)"}
+
+
 def oracle_rate(n_sample, max_seconds, threads=1, min_steps=1):
     """Aggregate cell-updates/s of `threads` oracle replicas, stepped until
     max_seconds have passed (and at least min_steps steps)."""
@@ -338,6 +353,11 @@ def jsonl_records(line, when=None):
         w = line["large_cfl_f2"]
         recs.append(dict(base, record="large_cfl_f2", gcell_s=w["gcell_s"], roofline_frac=w["roofline"]["frac"],
                          roundtrip_rel_l2=w["roundtrip_rel_l2"]))
+    if line.get("rayleigh_benard_f4"):
+        rb = line["rayleigh_benard_f4"]
+        recs.append(dict(base, record="rayleigh_benard_f4", grid=rb["grid"],
+                         **{k: {"us_per_step": v["us_per_step"], "top_reached_at_step": v["top_reached_at_step"]}
+                            for k, v in rb.items() if k in ("CIR", "FEC", "BEC", "CEC")}))
     return recs
 
 
@@ -483,6 +503,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         extras["large_cfl_f2"] = large_cfl_measurement(torch, sl, stream)
         extras["learned_c4"] = learned_measurement(torch, sl, stream)
+        extras["rayleigh_benard_f4"] = rb_measurement(torch, sl, stream)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -929,6 +950,47 @@ def deformation_measurement(torch, sl, stream, n=512, total_steps=2000, timed=20
     return {"grid": [n, n, n], "fields": 4, "steps_T": total_steps,
             "field_gcell_s": 4 * n ** 3 / (ms * 1e-3) / 1e9, "ms_per_step": ms,
             "rel_l2_at_T": {"u": errs[0], "v": errs[1], "w": errs[2], "scalar": errs[3]}}
+
+
+def rb_measurement(torch, sl, stream, n=50, Ra=1e5, dt=2e-5, steps=1000):
+    """The Sec. 6 run: Rayleigh-Benard box 2 x 1 on n x n cells, Pr = 1, the
+    +-0.1 spots near the lower left corner, U = 0, FP64, every scheme for
+    `steps` steps (the rising plume reaches the top after about a thousand).
+    Reports the time per step of sl_rb_step over the whole run, the first step
+    (to 10) at which theta > 0.02 reaches the top three rows, and the state's
+    extrema, total variation of theta and mean kinetic energy at the end (CIR
+    diffuses the plume: lower extrema and energy)."""
+    from paper_1606_06117_gb300 import workloads as W
+    th0 = torch.from_numpy(W.rb_spots(n, n)).cuda()
+    z0 = torch.zeros_like(th0)
+    out = {"grid": [n, n], "box": [2.0, 1.0], "Ra": Ra, "Pr": 1.0, "dt": dt, "steps": steps, "dtype": "f64"}
+    for name in ("CIR", "FEC", "BEC", "CEC"):
+        box = sl.RayleighBenard(n, n, Ra=Ra, scheme=name)
+        try:
+            box.set_state(z0, z0, th0)
+            box.step(dt, 10)   # warm-up
+            box.set_state(z0, z0, th0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            box.step(dt, steps)
+            torch.cuda.synchronize()
+            us = (time.perf_counter() - t0) / steps * 1e6
+            box.set_state(z0, z0, th0)
+            reach = None
+            for k in range(0, steps, 10):
+                box.step(dt, 10)
+                if reach is None and bool((box.state()[2][-3:] > 0.02).any()):
+                    reach = k + 10
+            u, w, th = box.state()
+            tv = float((th[1:] - th[:-1]).abs().sum() + (th[:, 1:] - th[:, :-1]).abs().sum())
+            out[name] = {"us_per_step": us, "top_reached_at_step": reach, "theta_max": float(th.max()),
+                         "theta_min": float(th.min()), "theta_tv": tv,
+                         "kinetic_energy": float(0.5 * (u * u + w * w).mean())}
+        finally:
+            box.close()
+    out["device_status"] = sl.sl_device_status()
+    out["cpu_baseline"] = rb_oracle_rate(n, Ra, dt)
+    return out
 
 
 def main():

@@ -464,6 +464,50 @@ int sl_advect_learned(sl_corrector *c, void *out, const void *in, const void *ve
                       const int64_t dims[3], const double spacing[3], double dt, int step_parity,
                       int check, double fallback_ratio, int *used_plain, double errs[2], void *stream);
 
+/* ------------------------------------------------------------------------
+ * Rayleigh-Benard box (Sec. 6, eqs. e:nsnd, e:Tnd, e:mnd, e:poisson, e:proj).
+ *
+ * A 2D box of nx x nz cells over Lx x Lz (x fastest, z upwards; the paper's
+ * box has Lz / Lx = 0.5, Pr = 1), no-slip impermeable walls, theta = 0 on the
+ * plates and d theta / dx = 0 on the side walls.  The state is the velocity
+ * U = (u, w) and the temperature perturbation theta, cell-centred.  One step
+ * from step n:
+ *   ghost layers (3 per side) of u, w, theta := the walls' mirror images
+ *     (u, w change sign across every wall, theta across the plates only);
+ *   (u1, w1, theta1) := the chosen scheme's step of u, w and theta by U^n on
+ *     the padded grid (the SL_CEC sweep order alternates with the step index);
+ *   u2 = u1 + dt Pr lap u^n, w2 = w1 + dt (Ra Pr theta^n + Pr lap w^n),
+ *   theta^{n+1} = theta1 + dt (w^n + lap theta^n)   (5-point Laplacians);
+ *   faces: averages of the adjacent cells of (u2, w2), zero on the walls;
+ *   lap phi = div faces with d phi / dn = 0, zero-mean phi;
+ *   U^{n+1} = U2 - (cell average of the two face gradients of phi).
+ * The projected faces are divergence-free up to rounding.
+ *
+ * sl_rb_create: nx, nz in [4, 4096]; Lx, Lz > 0; Ra finite; Pr >= 0;
+ *   scheme sl_scheme; dtype SL_F64 or SL_F32 (the arithmetic of every step).
+ *   Allocates all device buffers on the current device (about
+ *   12 (nx + 6)(nz + 6) + 3 nx nz + nx^2 + nz^2 elements); the state starts at
+ *   rest (U = 0, theta = 0).  Errors: SL_ERR_ARG, SL_ERR_UNSUPPORTED,
+ *   SL_ERR_NOMEM, SL_ERR_CUDA.
+ * sl_rb_set_state / sl_rb_get_state: DEVICE arrays of nz x nx elements of the
+ *   box's dtype (row-major, x fastest) for u, w and theta, copied in / out on
+ *   stream; set_state also resets the step index to 0.  Errors: SL_ERR_ARG.
+ * sl_rb_step: nsteps steps of size dt on stream (enqueued, not waited for).
+ *   The advection needs |u| dt / dx and |w| dt / dz below 1 (the kernels'
+ *   stencil reach; sl_device_status flags a violation).  Errors: SL_ERR_ARG
+ *   (NULL box, nsteps < 0, non-finite dt, a box of another device), and those
+ *   of sl_advect_multi.
+ * sl_rb_destroy: frees the box (NULL is a no-op); the caller makes sure none
+ *   of its steps is still running.
+ */
+typedef struct sl_rb sl_rb;
+int sl_rb_create(sl_rb **out, int nx, int nz, double Lx, double Lz, double Ra, double Pr, int scheme,
+                 int dtype);
+int sl_rb_set_state(sl_rb *rb, const void *u, const void *w, const void *theta, void *stream);
+int sl_rb_get_state(sl_rb *rb, void *u, void *w, void *theta, void *stream);
+int sl_rb_step(sl_rb *rb, double dt, int nsteps, void *stream);
+int sl_rb_destroy(sl_rb *rb);
+
 #ifdef __cplusplus
 }
 #endif

@@ -144,15 +144,3 @@ class Box:
         # the projected faces, for the divergence pin
         return uf - gx, wf - gz
 
-
-def initial_theta(nx, nz, Lx=2.0, Lz=1.0, amp=0.1, r=0.1, hot=(0.25, 0.2), cold=(0.5, 0.2)):
-    """The paper's start (Sec. 6): a hot spot (theta = +amp) next to a cold spot
-    (theta = -amp) near the lower left corner; here disks of radius r (in units
-    of Lz) centred at `hot` and `cold`, U = 0."""
-    x = (np.arange(nx) + 0.5) * (Lx / nx)
-    z = (np.arange(nz) + 0.5) * (Lz / nz)
-    X, Z = np.meshgrid(x, z)
-    th = np.zeros((nz, nx))
-    th[(X - hot[0]) ** 2 + (Z - hot[1]) ** 2 < r ** 2] = amp
-    th[(X - cold[0]) ** 2 + (Z - cold[1]) ** 2 < r ** 2] = -amp
-    return th

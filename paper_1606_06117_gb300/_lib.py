@@ -35,7 +35,8 @@ EXPORTS = ("sl_version", "sl_last_error", "sl_init", "sl_advect", "sl_advect_mul
            "sl_corrector_reset", "sl_advect_learned", "sl_selftest_wait_timeout", "sl_advect_wide_workspace",
            "sl_advect_wide", "sl_autotune_scheme", "sl_tuning_get", "sl_tuning_save", "sl_tuning_load",
            "sl_tuning_clear", "sl_batch_autotune", "sl_batch_tuning", "sl_field_save", "sl_field_load",
-           "sl_corrector_save", "sl_corrector_load")
+           "sl_corrector_save", "sl_corrector_load", "sl_rb_create", "sl_rb_set_state", "sl_rb_get_state",
+           "sl_rb_step", "sl_rb_destroy")
 KERNELS = {1: "cec_fast", 2: "cec_split", 3: "cir_groups", 4: "unsplit"}
 
 
@@ -121,6 +122,11 @@ def load(path: str | None = None):
             "sl_field_load": ([ctypes.c_char_p, vp, i, i64p, i, ctypes.POINTER(ctypes.c_int64), vp], i),
             "sl_corrector_save": ([vp, ctypes.c_char_p], i),
             "sl_corrector_load": ([vp, ctypes.c_char_p], i),
+            "sl_rb_create": ([ctypes.POINTER(vp), i, i, d, d, d, d, i, i], i),
+            "sl_rb_set_state": ([vp, vp, vp, vp, vp], i),
+            "sl_rb_get_state": ([vp, vp, vp, vp, vp], i),
+            "sl_rb_step": ([vp, d, i, vp], i),
+            "sl_rb_destroy": ([vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -457,3 +463,62 @@ def advect_wide(phi: torch.Tensor, vel: torch.Tensor, dt: float, spacing=None, s
         ws, nbytes = base + off, workspace.numel() * workspace.element_size() - off
     sl_advect_wide(out, phi, vel, ndim, dims, sp, dt, sc, dc, parity, ws, nbytes, stream)
     return out
+
+
+def sl_rb_create(nx, nz, Lx=2.0, Lz=1.0, Ra=1e5, Pr=1.0, scheme="CEC", dtype=F64):
+    h = ctypes.c_void_p()
+    sc = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    _check(load().sl_rb_create(ctypes.byref(h), int(nx), int(nz), float(Lx), float(Lz), float(Ra), float(Pr), sc,
+                               int(dtype)))
+    return h
+
+
+def sl_rb_set_state(rb, u, w, theta, stream=None):
+    return _check(load().sl_rb_set_state(rb, _ptr(u), _ptr(w), _ptr(theta), _stream(stream)))
+
+
+def sl_rb_get_state(rb, u, w, theta, stream=None):
+    return _check(load().sl_rb_get_state(rb, _ptr(u), _ptr(w), _ptr(theta), _stream(stream)))
+
+
+def sl_rb_step(rb, dt, nsteps=1, stream=None):
+    return _check(load().sl_rb_step(rb, float(dt), int(nsteps), _stream(stream)))
+
+
+def sl_rb_destroy(rb):
+    return _check(load().sl_rb_destroy(rb))
+
+
+class RayleighBenard:
+    """A Rayleigh-Benard box on the current CUDA device (sl_rb_*): the state
+    as (nz, nx) CUDA tensors of the box's dtype."""
+
+    def __init__(self, nx, nz, Lx=2.0, Lz=1.0, Ra=1e5, Pr=1.0, scheme="CEC", dtype=torch.float64):
+        self.nx, self.nz, self.dtype = nx, nz, dtype
+        self.h = sl_rb_create(nx, nz, Lx, Lz, Ra, Pr, scheme, dtype_code(dtype))
+
+    def set_state(self, u, w, theta):
+        t = [x.to(device="cuda", dtype=self.dtype).contiguous() for x in (u, w, theta)]
+        if any(x.shape != (self.nz, self.nx) for x in t):
+            raise ValueError("u, w and theta must be (nz, nx)")
+        sl_rb_set_state(self.h, *t)
+        torch.cuda.current_stream().synchronize()
+
+    def state(self):
+        out = [torch.empty((self.nz, self.nx), dtype=self.dtype, device="cuda") for _ in range(3)]
+        sl_rb_get_state(self.h, *out)
+        return out
+
+    def step(self, dt, nsteps=1):
+        sl_rb_step(self.h, dt, nsteps)
+
+    def close(self):
+        if self.h is not None:
+            sl_rb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,393 @@
+// k_rb.cu -- the Rayleigh-Benard driver of Sec. 6 (eqs. e:nsnd, e:Tnd, e:mnd,
+// e:poisson, e:proj) on the GPU: a 2D box with walls on all four sides, the
+// velocity U = (u, w) and the temperature perturbation theta advected
+// semi-Lagrangian by U with one of the paper's schemes, explicit buoyancy and
+// diffusion, and a pressure-correction projection.
+//
+// Discretisation (cell-centred, nx x nz cells of Lx x Lz):
+//  * the fields live on a grid padded by G = 3 ghost layers (the reach of the
+//    split CEC stencil); before each step the ghosts are the walls' mirror
+//    images: u and w change sign across every wall (no slip), theta changes
+//    sign across the plates (theta = 0) and keeps it across the side walls
+//    (d theta / dx = 0);
+//  * the advection is sl_advect on the padded grid with the padded velocity:
+//    the periodic wrap of the step kernels only ever reaches ghost cells;
+//  * u2 = L[u] + dt Pr lap u, w2 = L[w] + dt (Ra Pr theta + Pr lap w),
+//    theta' = L[theta] + dt (w + lap theta), 5-point Laplacians of the step-n
+//    fields;
+//  * projection: face velocities are averages of the two adjacent cells (zero
+//    on the walls), their divergence D is the right-hand side of lap phi = D
+//    with the compact Neumann Laplacian, solved in its eigenbasis: the
+//    orthonormal DCT-II matrices C_x, C_z diagonalise it with eigenvalues
+//    -(4/h^2) sin^2(pi j / 2 n) per axis, so phi = C_z^T [(C_z D C_x^T) / lam] C_x
+//    with the constant mode set to zero (four small dense products).  Cells
+//    take the average of their two faces' gradient corrections.
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "sl.h"
+#include "sl_internal.h"
+
+namespace sl {
+namespace {
+
+constexpr int RBG = 3;   // ghost layers
+
+// Ghost cell (k, i) of a padded (nz + 2G) x (nx + 2G) plane: the mirror image
+// of an interior cell across the nearer wall(s), with sign sx per side-wall
+// crossing and sz per plate crossing.  Interior cells are left alone.
+template <typename T>
+__global__ void k_rb_ghosts(T *p, int nplanes, int nx, int nz, int64_t pstride, const int *sx, const int *sz)
+{
+    const int px = nx + 2 * RBG, pz = nz + 2 * RBG;
+    const int64_t n = (int64_t)px * pz;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * nplanes;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int f = (int)(idx / n);
+        const int64_t r = idx - (int64_t)f * n;
+        const int k = (int)(r / px), i = (int)(r - (int64_t)k * px);
+        const int ki = k - RBG, ii = i - RBG;
+        const bool gk = ki < 0 || ki >= nz, gi = ii < 0 || ii >= nx;
+        if (!gk && !gi) continue;
+        const int mk = ki < 0 ? -1 - ki : (ki >= nz ? 2 * nz - 1 - ki : ki);
+        const int mi = ii < 0 ? -1 - ii : (ii >= nx ? 2 * nx - 1 - ii : ii);
+        const int s = (gk ? sz[f] : 1) * (gi ? sx[f] : 1);
+        T *pl = p + f * pstride;
+        pl[r] = T(s) * pl[(int64_t)(mk + RBG) * px + mi + RBG];
+    }
+}
+
+// The explicit forces on the interior, from the advected fields a* and the
+// step-n fields (ghosts filled): u2, w2 into o_u, o_w; theta' into o_t.
+template <typename T>
+__global__ void k_rb_forces(const T *u, const T *w, const T *th, const T *au, const T *aw, const T *at, T *o_u, T *o_w,
+                            T *o_t, int nx, int nz, T dt, T Ra, T Pr, T idx2, T idz2)
+{
+    const int px = nx + 2 * RBG;
+    const int n = nx * nz;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const int k = c / nx, i = c - (c / nx) * nx;
+        const int64_t o = (int64_t)(k + RBG) * px + i + RBG;
+        auto lap = [&](const T *f) {
+            return (f[o + 1] - T(2) * f[o] + f[o - 1]) * idx2 + (f[o + px] - T(2) * f[o] + f[o - px]) * idz2;
+        };
+        o_u[o] = au[o] + dt * (Pr * lap(u));
+        o_w[o] = aw[o] + dt * (Ra * Pr * th[o] + Pr * lap(w));
+        o_t[o] = at[o] + dt * (w[o] + lap(th));
+    }
+}
+
+// Divergence of the face velocities (averages of the adjacent cells, zero on
+// the walls) at every interior cell, into d (nz x nx, row-major).
+template <typename T>
+__global__ void k_rb_div(const T *u2, const T *w2, T *d, int nx, int nz, T idx, T idz)
+{
+    const int px = nx + 2 * RBG;
+    const int n = nx * nz;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const int k = c / nx, i = c - (c / nx) * nx;
+        const int64_t o = (int64_t)(k + RBG) * px + i + RBG;
+        const T ue = i + 1 < nx ? T(0.5) * (u2[o] + u2[o + 1]) : T(0);
+        const T uw = i > 0 ? T(0.5) * (u2[o - 1] + u2[o]) : T(0);
+        const T wn = k + 1 < nz ? T(0.5) * (w2[o] + w2[o + px]) : T(0);
+        const T ws = k > 0 ? T(0.5) * (w2[o - px] + w2[o]) : T(0);
+        d[c] = (ue - uw) * idx + (wn - ws) * idz;
+    }
+}
+
+// C = op(A) op(B) for small dense row-major matrices (M x N result, inner K):
+// op(A)[m][k] = TA ? A[k][m] : A[m][k], same for B.  Tiles of 16 x 16.
+template <typename T, bool TA, bool TB>
+__global__ void k_rb_gemm(const T *A, const T *B, T *C, int M, int N, int K, int lda, int ldb, int ldc)
+{
+    __shared__ T sa[16][17], sb[16][17];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int m = blockIdx.y * 16 + ty, nn = blockIdx.x * 16 + tx;
+    T acc = T(0);
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        const int ka = k0 + tx, kb = k0 + ty;
+        const int am = blockIdx.y * 16 + ty, bn = blockIdx.x * 16 + tx;
+        sa[ty][tx] = (am < M && ka < K) ? (TA ? A[(int64_t)ka * lda + am] : A[(int64_t)am * lda + ka]) : T(0);
+        sb[ty][tx] = (kb < K && bn < N) ? (TB ? B[(int64_t)bn * ldb + kb] : B[(int64_t)kb * ldb + bn]) : T(0);
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) acc += sa[ty][kk] * sb[kk][tx];
+        __syncthreads();
+    }
+    if (m < M && nn < N) C[(int64_t)m * ldc + nn] = acc;
+}
+
+// F[k][j] /= (lz[k] + lx[j]); the constant mode is set to zero.
+template <typename T>
+__global__ void k_rb_scale(T *F, const T *lx, const T *lz, int nx, int nz)
+{
+    const int n = nx * nz;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const int k = c / nx, j = c - (c / nx) * nx;
+        F[c] = c == 0 ? T(0) : F[c] / (lz[k] + lx[j]);
+    }
+}
+
+// Projection: cells take the average of their two faces' gradient corrections
+// (face gradient (phi_{i+1} - phi_i) / dx inside, zero on the walls); the
+// result is the new u, w (interior of the padded state).
+template <typename T>
+__global__ void k_rb_project(const T *u2, const T *w2, const T *phi, T *u, T *w, int nx, int nz, T idx, T idz)
+{
+    const int px = nx + 2 * RBG;
+    const int n = nx * nz;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const int k = c / nx, i = c - (c / nx) * nx;
+        const int64_t o = (int64_t)(k + RBG) * px + i + RBG;
+        const T ge = i + 1 < nx ? (phi[c + 1] - phi[c]) * idx : T(0);
+        const T gw = i > 0 ? (phi[c] - phi[c - 1]) * idx : T(0);
+        const T gn = k + 1 < nz ? (phi[c + nx] - phi[c]) * idz : T(0);
+        const T gs = k > 0 ? (phi[c] - phi[c - nx]) * idz : T(0);
+        u[o] = u2[o] - T(0.5) * (gw + ge);
+        w[o] = w2[o] - T(0.5) * (gs + gn);
+    }
+}
+
+// interior <-> padded copies
+template <typename T>
+__global__ void k_rb_copy(const T *src, T *dst, int nx, int nz, bool to_padded)
+{
+    const int px = nx + 2 * RBG;
+    const int n = nx * nz;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const int k = c / nx, i = c - (c / nx) * nx;
+        const int64_t o = (int64_t)(k + RBG) * px + i + RBG;
+        if (to_padded)
+            dst[o] = src[c];
+        else
+            dst[c] = src[o];
+    }
+}
+
+int blocks_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
+
+}  // namespace
+}  // namespace sl
+
+using namespace sl;
+
+struct sl_rb {
+    int device = -1;
+    int nx = 0, nz = 0, scheme = SL_CEC, dtype = SL_F64;
+    double Lx = 2.0, Lz = 1.0, Ra = 0.0, Pr = 1.0;
+    int64_t step = 0;
+    size_t esz = 8;
+    int64_t plane = 0;     // padded plane: (nx + 2G) (nz + 2G) elements
+    int cur = 0;           // which of the two state buffers holds step n
+    void *mem = nullptr;   // one device allocation
+    // padded planes: two states (u, w, theta back to back, so that (u, w) is
+    // the velocity argument of the advection), the advected fields, (u2, w2)
+    void *S[2] = {nullptr, nullptr}, *A = nullptr, *W = nullptr;
+    // interior arrays: divergence / transform work, phi
+    void *d = nullptr, *t1 = nullptr, *phi = nullptr;
+    void *cx = nullptr, *cz = nullptr, *lx = nullptr, *lz = nullptr;   // DCT matrices, eigenvalues
+    int *signs = nullptr;   // sx of (u, w, theta), then sz of (u, w, theta)
+};
+
+namespace {
+
+template <typename T>
+int rb_step_t(sl_rb *r, double dt, int nsteps, cudaStream_t st)
+{
+    const int nx = r->nx, nz = r->nz, n = nx * nz;
+    const int px = nx + 2 * RBG, pz = nz + 2 * RBG;
+    const int64_t P = r->plane;
+    T *A = static_cast<T *>(r->A), *Wk = static_cast<T *>(r->W);
+    T *d = static_cast<T *>(r->d), *t1 = static_cast<T *>(r->t1), *phi = static_cast<T *>(r->phi);
+    const T *cx = static_cast<const T *>(r->cx), *cz = static_cast<const T *>(r->cz);
+    const T *lx = static_cast<const T *>(r->lx), *lz = static_cast<const T *>(r->lz);
+    const double dx = r->Lx / nx, dz = r->Lz / nz;
+    const int64_t pdims[3] = {px, pz, 1};
+    const double sp[3] = {dx, dz, 1.0};
+    const int gb = blocks_for(P * 3), cb = blocks_for(n);
+    const dim3 gblk(16, 16);
+    auto grid2 = [](int M, int N) { return dim3((N + 15) / 16, (M + 15) / 16); };
+    for (int s = 0; s < nsteps; ++s) {
+        T *S0 = static_cast<T *>(r->S[r->cur]), *S1 = static_cast<T *>(r->S[r->cur ^ 1]);
+        // the walls' mirror images in the ghost layers of u, w, theta
+        k_rb_ghosts<T><<<gb, 256, 0, st>>>(S0, 3, nx, nz, P, r->signs, r->signs + 3);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return set_error(SL_ERR_CUDA, cudaGetErrorString(e));
+        // semi-Lagrangian advection of u, w, theta by U^n on the padded box;
+        // CEC alternates its sweep order with the step index
+        const void *ins[3] = {S0, S0 + P, S0 + 2 * P};
+        void *outs[3] = {A, A + P, A + 2 * P};
+        int rc = sl_advect_multi(outs, ins, 3, S0, 2, pdims, sp, dt, r->scheme, r->dtype, (int)(r->step & 1), st);
+        if (rc) return rc;
+        // forces: u2, w2 into the work planes, theta' straight into the next state
+        k_rb_forces<T><<<cb, 256, 0, st>>>(S0, S0 + P, S0 + 2 * P, A, A + P, A + 2 * P, Wk, Wk + P, S1 + 2 * P, nx,
+                                           nz, T(dt), T(r->Ra), T(r->Pr), T(1.0 / (dx * dx)), T(1.0 / (dz * dz)));
+        k_rb_div<T><<<cb, 256, 0, st>>>(Wk, Wk + P, d, nx, nz, T(1.0 / dx), T(1.0 / dz));
+        // phi = C_z^T [(C_z D C_x^T) / lam] C_x
+        k_rb_gemm<T, false, false><<<grid2(nz, nx), gblk, 0, st>>>(cz, d, t1, nz, nx, nz, nz, nx, nx);
+        k_rb_gemm<T, false, true><<<grid2(nz, nx), gblk, 0, st>>>(t1, cx, d, nz, nx, nx, nx, nx, nx);
+        k_rb_scale<T><<<cb, 256, 0, st>>>(d, lx, lz, nx, nz);
+        k_rb_gemm<T, true, false><<<grid2(nz, nx), gblk, 0, st>>>(cz, d, t1, nz, nx, nz, nz, nx, nx);
+        k_rb_gemm<T, false, false><<<grid2(nz, nx), gblk, 0, st>>>(t1, cx, phi, nz, nx, nx, nx, nx, nx);
+        // the projected u, w of the next state
+        k_rb_project<T><<<cb, 256, 0, st>>>(Wk, Wk + P, phi, S1, S1 + P, nx, nz, T(1.0 / dx), T(1.0 / dz));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return set_error(SL_ERR_CUDA, cudaGetErrorString(e));
+        r->cur ^= 1;
+        ++r->step;
+    }
+    return SL_OK;
+}
+
+template <typename T>
+int rb_copy_t(sl_rb *r, const void *u, const void *w, const void *t, void *ou, void *ow, void *ot, cudaStream_t st)
+{
+    const int cb = blocks_for((int64_t)r->nx * r->nz);
+    T *S = static_cast<T *>(r->S[r->cur]);
+    const int64_t P = r->plane;
+    if (u) {
+        k_rb_copy<T><<<cb, 256, 0, st>>>(static_cast<const T *>(u), S, r->nx, r->nz, true);
+        k_rb_copy<T><<<cb, 256, 0, st>>>(static_cast<const T *>(w), S + P, r->nx, r->nz, true);
+        k_rb_copy<T><<<cb, 256, 0, st>>>(static_cast<const T *>(t), S + 2 * P, r->nx, r->nz, true);
+    } else {
+        k_rb_copy<T><<<cb, 256, 0, st>>>(S, static_cast<T *>(ou), r->nx, r->nz, false);
+        k_rb_copy<T><<<cb, 256, 0, st>>>(S + P, static_cast<T *>(ow), r->nx, r->nz, false);
+        k_rb_copy<T><<<cb, 256, 0, st>>>(S + 2 * P, static_cast<T *>(ot), r->nx, r->nz, false);
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SL_OK : set_error(SL_ERR_CUDA, cudaGetErrorString(e));
+}
+
+// orthonormal DCT-II matrix, row j: s_j cos(pi j (i + 1/2) / n)
+void dct_matrix(std::vector<double> &c, int n)
+{
+    c.resize((size_t)n * n);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i)
+            c[(size_t)j * n + i] = std::sqrt((j == 0 ? 1.0 : 2.0) / n) * std::cos(M_PI * j * (i + 0.5) / n);
+}
+
+}  // namespace
+
+extern "C" {
+
+int sl_rb_create(sl_rb **out, int nx, int nz, double Lx, double Lz, double Ra, double Pr, int scheme, int dtype)
+{
+    if (!out) return set_error(SL_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 4 || nz < 4 || nx > 4096 || nz > 4096) return set_error(SL_ERR_ARG, "nx and nz must be in [4, 4096]");
+    if (!(Lx > 0) || !(Lz > 0) || !std::isfinite(Lx) || !std::isfinite(Lz) || !std::isfinite(Ra) ||
+        !std::isfinite(Pr) || Pr < 0)
+        return set_error(SL_ERR_ARG, "Lx, Lz must be > 0; Ra, Pr finite, Pr >= 0");
+    if (scheme < SL_CIR || scheme > SL_CEC) return set_error(SL_ERR_ARG, "unknown scheme");
+    if (dtype != SL_F32 && dtype != SL_F64) return set_error(SL_ERR_UNSUPPORTED, "the box runs in SL_F32 or SL_F64");
+    DevCtx *c = ctx_get();
+    if (!c) return set_error(SL_ERR_CUDA, "could not create the device context");
+    sl_rb *r = new (std::nothrow) sl_rb();
+    if (!r) return set_error(SL_ERR_NOMEM, "host allocation");
+    r->device = c->device;
+    r->nx = nx;
+    r->nz = nz;
+    r->Lx = Lx;
+    r->Lz = Lz;
+    r->Ra = Ra;
+    r->Pr = Pr;
+    r->scheme = scheme;
+    r->dtype = dtype;
+    r->esz = dtype == SL_F64 ? 8 : 4;
+    // the planes of one state are contiguous (the advection's velocity is
+    // (u, w)); every buffer starts on a 512-byte boundary
+    r->plane = (int64_t)(nx + 2 * RBG) * (nz + 2 * RBG);
+    auto round64 = [](int64_t k) { return (k + 63) / 64 * 64; };
+    const int64_t n = (int64_t)nx * nz;
+    const int64_t elems = 4 * round64(3 * r->plane) + 3 * round64(n) + round64((int64_t)nx * nx) +
+                          round64((int64_t)nz * nz) + round64(nx) + round64(nz) + 64;
+    if (cudaMalloc(&r->mem, r->esz * elems) != cudaSuccess) {
+        delete r;
+        return set_error(SL_ERR_NOMEM, "device buffers of the box");
+    }
+    char *p = static_cast<char *>(r->mem);
+    auto take = [&](int64_t k) {
+        void *q = p;
+        p += r->esz * round64(k);
+        return q;
+    };
+    r->S[0] = take(3 * r->plane);
+    r->S[1] = take(3 * r->plane);
+    r->A = take(3 * r->plane);
+    r->W = take(3 * r->plane);
+    r->d = take(n);
+    r->t1 = take(n);
+    r->phi = take(n);
+    r->cx = take((int64_t)nx * nx);
+    r->cz = take((int64_t)nz * nz);
+    r->lx = take(nx);
+    r->lz = take(nz);
+    r->signs = reinterpret_cast<int *>(p);
+    std::vector<double> cxm, czm, lxv(nx), lzv(nz);
+    dct_matrix(cxm, nx);
+    dct_matrix(czm, nz);
+    const double dx = Lx / nx, dz = Lz / nz;
+    for (int j = 0; j < nx; ++j) lxv[j] = -4.0 / (dx * dx) * std::pow(std::sin(M_PI * j / (2.0 * nx)), 2);
+    for (int k = 0; k < nz; ++k) lzv[k] = -4.0 / (dz * dz) * std::pow(std::sin(M_PI * k / (2.0 * nz)), 2);
+    const int signs[6] = {-1, -1, 1, -1, -1, -1};   // sx of u, w, theta; sz of u, w, theta
+    cudaError_t e = cudaMemset(r->mem, 0, r->esz * elems);
+    auto up = [&](void *dst, const std::vector<double> &v) {
+        if (e != cudaSuccess) return;
+        if (dtype == SL_F64) {
+            e = cudaMemcpy(dst, v.data(), 8 * v.size(), cudaMemcpyHostToDevice);
+        } else {
+            const std::vector<float> f(v.begin(), v.end());
+            e = cudaMemcpy(dst, f.data(), 4 * f.size(), cudaMemcpyHostToDevice);
+        }
+    };
+    up(r->cx, cxm);
+    up(r->cz, czm);
+    up(r->lx, lxv);
+    up(r->lz, lzv);
+    if (e == cudaSuccess) e = cudaMemcpy(r->signs, signs, sizeof signs, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(r->mem);
+        delete r;
+        return set_error(SL_ERR_CUDA, cudaGetErrorString(e));
+    }
+    *out = r;
+    return SL_OK;
+}
+
+int sl_rb_set_state(sl_rb *r, const void *u, const void *w, const void *theta, void *stream)
+{
+    if (!r || !u || !w || !theta) return set_error(SL_ERR_ARG, "NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    r->step = 0;
+    return r->dtype == SL_F64 ? rb_copy_t<double>(r, u, w, theta, nullptr, nullptr, nullptr, st)
+                              : rb_copy_t<float>(r, u, w, theta, nullptr, nullptr, nullptr, st);
+}
+
+int sl_rb_get_state(sl_rb *r, void *u, void *w, void *theta, void *stream)
+{
+    if (!r || !u || !w || !theta) return set_error(SL_ERR_ARG, "NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return r->dtype == SL_F64 ? rb_copy_t<double>(r, nullptr, nullptr, nullptr, u, w, theta, st)
+                              : rb_copy_t<float>(r, nullptr, nullptr, nullptr, u, w, theta, st);
+}
+
+int sl_rb_step(sl_rb *r, double dt, int nsteps, void *stream)
+{
+    if (!r || nsteps < 0 || !std::isfinite(dt)) return set_error(SL_ERR_ARG, "bad argument");
+    DevCtx *c = ctx_get();
+    if (!c || c->device != r->device) return set_error(SL_ERR_ARG, "the box belongs to another device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return r->dtype == SL_F64 ? rb_step_t<double>(r, dt, nsteps, st) : rb_step_t<float>(r, dt, nsteps, st);
+}
+
+int sl_rb_destroy(sl_rb *r)
+{
+    if (!r) return SL_OK;
+    if (r->mem) cudaFree(r->mem);
+    delete r;
+    return SL_OK;
+}
+
+}  // extern "C"

@@ -293,3 +293,19 @@ def instance_fields(inst: Instance, device="cpu", dtype=torch.float32, nmodes=32
     else:
         vel = taylor_green_velocity(shape, inst.amps[0], device=device, dtype=dtype)
     return phi, vel
+
+
+# ------------------------------------------------------------- Rayleigh-Benard
+def rb_spots(nx, nz, Lx=2.0, Lz=1.0, amp=0.1, r=0.1, hot=(0.25, 0.2), cold=(0.5, 0.2)):
+    """The start of the Sec. 6 runs: a hot spot (theta = +amp) next to a cold
+    spot (theta = -amp) near the lower left corner of the box [0, Lx] x [0, Lz]
+    (walls, not periodic), U = 0.  Here disks of radius r (in units of Lz)
+    centred at ``hot`` and ``cold``, on the cell centres of nx x nz cells;
+    returns a (nz, nx) float64 numpy array."""
+    x = (np.arange(nx) + 0.5) * (Lx / nx)
+    z = (np.arange(nz) + 0.5) * (Lz / nz)
+    X, Z = np.meshgrid(x, z)
+    th = np.zeros((nz, nx))
+    th[(X - hot[0]) ** 2 + (Z - hot[1]) ** 2 < r ** 2] = amp
+    th[(X - cold[0]) ** 2 + (Z - cold[1]) ** 2 < r ** 2] = -amp
+    return th

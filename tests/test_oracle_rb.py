@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from oracle import rb_oracle as R
+from paper_1606_06117_gb300 import workloads as W
 
 
 def test_ghost_fill_mirrors_across_each_wall():
@@ -78,7 +79,7 @@ def test_mirror_symmetric_start_stays_mirror_symmetric(scheme):
     """theta symmetric about x = Lx / 2 and U = 0: theta and w stay symmetric
     and u antisymmetric (the box and the equations are invariant under x -> Lx - x)."""
     nx, nz = 20, 10
-    th = R.initial_theta(nx, nz, hot=(1.0, 0.25), cold=(1.0, 0.6), r=0.15)
+    th = W.rb_spots(nx, nz, hot=(1.0, 0.25), cold=(1.0, 0.6), r=0.15)
     th = 0.5 * (th + th[:, ::-1])                     # exactly symmetric (x_i - 1 rounds unevenly)
     assert np.array_equal(th, th[:, ::-1]) and th.any()
     box = R.Box(nx, nz, Ra=5e4, scheme=scheme)
@@ -94,7 +95,7 @@ def test_buoyancy_lifts_the_hot_spot():
     """A hot spot starts rising: after a few steps w > 0 over it, w < 0 over the cold one."""
     nx, nz = 24, 12
     box = R.Box(nx, nz, Ra=1e5, scheme="CEC")
-    box.theta = R.initial_theta(nx, nz)
+    box.theta = W.rb_spots(nx, nz)
     for _ in range(10):
         box.step(1e-4)
     x = (np.arange(nx) + 0.5) * box.dx
