@@ -51,6 +51,10 @@ def parse():
                     help="only run warmup + steps wide CEC steps (CFL 3.64) on the workload, for ncu")
     ap.add_argument("--profile-learned", action="store_true",
                     help="only warm-up and timed learned-corrector steps (untrained weights; for ncu)")
+    ap.add_argument("--profile-rb", action="store_true",
+                    help="only the Rayleigh-Benard run (50x50, every scheme, 1000 steps each; for ncu); prints "
+                         "its record")
+    ap.add_argument("--rb-steps", type=int, default=1000, help="steps of each --profile-rb run")
     ap.add_argument("--scheme", choices=["CIR", "FEC", "BEC", "CEC"], default="CEC",
                     help="scheme of the --profile steps")
     ap.add_argument("--jsonl", default=None,
@@ -952,7 +956,7 @@ def deformation_measurement(torch, sl, stream, n=512, total_steps=2000, timed=20
             "rel_l2_at_T": {"u": errs[0], "v": errs[1], "w": errs[2], "scalar": errs[3]}}
 
 
-def rb_measurement(torch, sl, stream, n=50, Ra=1e5, dt=2e-5, steps=1000):
+def rb_measurement(torch, sl, stream, n=50, Ra=1e5, dt=2e-5, steps=1000, cpu=True):
     """The Sec. 6 run: Rayleigh-Benard box 2 x 1 on n x n cells, Pr = 1, the
     +-0.1 spots near the lower left corner, U = 0, FP64, every scheme for
     `steps` steps (the rising plume reaches the top after about a thousand).
@@ -968,7 +972,7 @@ def rb_measurement(torch, sl, stream, n=50, Ra=1e5, dt=2e-5, steps=1000):
         box = sl.RayleighBenard(n, n, Ra=Ra, scheme=name)
         try:
             box.set_state(z0, z0, th0)
-            box.step(dt, 10)   # warm-up
+            box.step(dt, 16)   # warm-up (captures the replayed graph)
             box.set_state(z0, z0, th0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -989,13 +993,19 @@ def rb_measurement(torch, sl, stream, n=50, Ra=1e5, dt=2e-5, steps=1000):
         finally:
             box.close()
     out["device_status"] = sl.sl_device_status()
-    out["cpu_baseline"] = rb_oracle_rate(n, Ra, dt)
+    if cpu:
+        out["cpu_baseline"] = rb_oracle_rate(n, Ra, dt)
     return out
 
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_rb:
+        import torch
+        from paper_1606_06117_gb300 import _lib as sl
+        sl.load()
+        print(json.dumps(rb_measurement(torch, sl, None, steps=args.rb_steps, cpu=False)), flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -114,7 +114,10 @@ int sl_advect(void *out, const void *in, const void *vel, int ndim,
  * geometry of the persistent kernel (see sl_autotune) advances up to 4 fields
  * per launch: the launch's CTAs form groups, one CTA per field, that walk the
  * same (column tile, plane) sequence, so that a group's velocity reads can be
- * served from L2 after the first one.
+ * served from L2 after the first one.  Otherwise fields stored at uniform
+ * strides (ins[f] = ins[0] + f * a, outs[f] = outs[0] + f * b, whole elements)
+ * whose buffers share one 16-byte alignment run in one launch of the generic
+ * kernels, a row of CTAs per field; other field sets take a launch per field.
  */
 int sl_advect_multi(void *const *outs, const void *const *ins, int nfields,
                     const void *vel, int ndim, const int64_t dims[3],
@@ -486,13 +489,16 @@ int sl_advect_learned(sl_corrector *c, void *out, const void *in, const void *ve
  * sl_rb_create: nx, nz in [4, 4096]; Lx, Lz > 0; Ra finite; Pr >= 0;
  *   scheme sl_scheme; dtype SL_F64 or SL_F32 (the arithmetic of every step).
  *   Allocates all device buffers on the current device (about
- *   12 (nx + 6)(nz + 6) + 3 nx nz + nx^2 + nz^2 elements); the state starts at
+ *   12 (nx + 6)(nz + 6) + 3 nx nz + 2 nx^2 + nz^2 elements); the state starts at
  *   rest (U = 0, theta = 0).  Errors: SL_ERR_ARG, SL_ERR_UNSUPPORTED,
  *   SL_ERR_NOMEM, SL_ERR_CUDA.
  * sl_rb_set_state / sl_rb_get_state: DEVICE arrays of nz x nx elements of the
  *   box's dtype (row-major, x fastest) for u, w and theta, copied in / out on
  *   stream; set_state also resets the step index to 0.  Errors: SL_ERR_ARG.
  * sl_rb_step: nsteps steps of size dt on stream (enqueued, not waited for).
+ *   Runs of 16 steps or more replay a CUDA graph of 8 steps, captured on the
+ *   box's own stream for this dt (again when dt changes); the results equal
+ *   those of single steps bit for bit.
  *   The advection needs |u| dt / dx and |w| dt / dz below 1 (the kernels'
  *   stencil reach; sl_device_status flags a violation).  Errors: SL_ERR_ARG
  *   (NULL box, nsteps < 0, non-finite dt, a box of another device), and those

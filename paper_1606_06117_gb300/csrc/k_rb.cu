@@ -20,8 +20,17 @@
 //    with the compact Neumann Laplacian, solved in its eigenbasis: the
 //    orthonormal DCT-II matrices C_x, C_z diagonalise it with eigenvalues
 //    -(4/h^2) sin^2(pi j / 2 n) per axis, so phi = C_z^T [(C_z D C_x^T) / lam] C_x
-//    with the constant mode set to zero (four small dense products).  Cells
-//    take the average of their two faces' gradient corrections.
+//    with the constant mode set to zero.  Cells take the average of their
+//    two faces' gradient corrections.
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate (about two FMAs per
+// clock and SM), so the step is arranged to spend few FP64 operations and to
+// spread them over many SMs: each producer writes its cells' ghost images
+// itself (no separate fill pass), the forces kernel also gives the divergence,
+// the transforms run one CTA per mode row with coalesced or broadcast loads,
+// the per-cell kernels use small CTAs, and long runs replay the step from a
+// CUDA graph (7 launches per step: 3 advections, forces, two transforms,
+// projection).
 #include <cmath>
 #include <new>
 #include <vector>
@@ -34,13 +43,18 @@ namespace {
 
 constexpr int RBG = 3;   // ghost layers
 
+// Padded row length: G ghost columns on the left, G on the right and one more
+// there when nx is odd, so that a padded plane has an even number of cells
+// and the three state planes, back to back, share one 16-byte alignment.
+__host__ __device__ constexpr int rb_px(int nx) { return nx + 2 * RBG + (nx & 1); }
+
 // Ghost cell (k, i) of a padded (nz + 2G) x (nx + 2G) plane: the mirror image
 // of an interior cell across the nearer wall(s), with sign sx per side-wall
 // crossing and sz per plate crossing.  Interior cells are left alone.
 template <typename T>
 __global__ void k_rb_ghosts(T *p, int nplanes, int nx, int nz, int64_t pstride, const int *sx, const int *sz)
 {
-    const int px = nx + 2 * RBG, pz = nz + 2 * RBG;
+    const int px = rb_px(nx), pz = nz + 2 * RBG;
     const int64_t n = (int64_t)px * pz;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * nplanes;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -58,84 +72,133 @@ __global__ void k_rb_ghosts(T *p, int nplanes, int nx, int nz, int64_t pstride, 
     }
 }
 
-// The explicit forces on the interior, from the advected fields a* and the
-// step-n fields (ghosts filled): u2, w2 into o_u, o_w; theta' into o_t.
+// Stores v at interior cell (k, i) of a padded plane and at each ghost cell
+// whose mirror image it is (sign sx per side-wall crossing, sz per plate
+// crossing): the same values the ghost fill gives, written by the producer.
 template <typename T>
-__global__ void k_rb_forces(const T *u, const T *w, const T *th, const T *au, const T *aw, const T *at, T *o_u, T *o_w,
-                            T *o_t, int nx, int nz, T dt, T Ra, T Pr, T idx2, T idz2)
+__device__ __forceinline__ void store_mirrored(T *pl, int k, int i, T v, int nx, int nz, T sx, T sz)
 {
-    const int px = nx + 2 * RBG;
-    const int n = nx * nz;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        const int k = c / nx, i = c - (c / nx) * nx;
-        const int64_t o = (int64_t)(k + RBG) * px + i + RBG;
-        auto lap = [&](const T *f) {
-            return (f[o + 1] - T(2) * f[o] + f[o - 1]) * idx2 + (f[o + px] - T(2) * f[o] + f[o - px]) * idz2;
-        };
-        o_u[o] = au[o] + dt * (Pr * lap(u));
-        o_w[o] = aw[o] + dt * (Ra * Pr * th[o] + Pr * lap(w));
-        o_t[o] = at[o] + dt * (w[o] + lap(th));
-    }
+    const int px = rb_px(nx), gr = px - nx - RBG;   // gr ghost columns on the right
+    pl[(int64_t)(k + RBG) * px + i + RBG] = v;
+    const int gi = i < RBG ? -1 - i : (i >= nx - gr ? 2 * nx - 1 - i : INT32_MIN);
+    const int gk = k < RBG ? -1 - k : (k >= nz - RBG ? 2 * nz - 1 - k : INT32_MIN);
+    // a cell near both side walls (small nx) has two x images
+    const int gi2 = (i < RBG && i >= nx - gr) ? 2 * nx - 1 - i : INT32_MIN;
+    const int gk2 = (k < RBG && k >= nz - RBG) ? 2 * nz - 1 - k : INT32_MIN;
+    const int xs[3] = {i, gi, gi2}, zs[3] = {k, gk, gk2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if ((a == 0 && b == 0) || xs[a] == INT32_MIN || zs[b] == INT32_MIN) continue;
+            const T sg = (a ? sx : T(1)) * (b ? sz : T(1));
+            pl[(int64_t)(zs[b] + RBG) * px + xs[a] + RBG] = sg * v;
+        }
 }
 
-// Divergence of the face velocities (averages of the adjacent cells, zero on
-// the walls) at every interior cell, into d (nz x nx, row-major).
+// The explicit forces on the interior, from the advected fields a* and the
+// step-n fields (ghosts filled): u2, w2 into o_u, o_w (interior only),
+// theta' into o_t with its ghost images, and the divergence of the face
+// velocities (averages of the adjacent cells of (u2, w2), zero on the walls)
+// into d (nz x nx).  A cell evaluates u2 and w2 of its neighbours itself (the
+// same expressions), so that no second pass is needed for the divergence.
 template <typename T>
-__global__ void k_rb_div(const T *u2, const T *w2, T *d, int nx, int nz, T idx, T idz)
+__global__ void k_rb_forces(const T *u, const T *w, const T *th, const T *au, const T *aw, const T *at, T *o_u, T *o_w,
+                            T *o_t, T *d, int nx, int nz, T dt, T Ra, T Pr, T idx2, T idz2, T idx, T idz)
 {
-    const int px = nx + 2 * RBG;
+    const int px = rb_px(nx);
     const int n = nx * nz;
+    auto lap = [&](const T *f, int64_t o) {
+        return (f[o + 1] - T(2) * f[o] + f[o - 1]) * idx2 + (f[o + px] - T(2) * f[o] + f[o - px]) * idz2;
+    };
+    auto u2 = [&](int64_t o) { return au[o] + dt * (Pr * lap(u, o)); };
+    auto w2 = [&](int64_t o) { return aw[o] + dt * (Ra * Pr * th[o] + Pr * lap(w, o)); };
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         const int k = c / nx, i = c - (c / nx) * nx;
         const int64_t o = (int64_t)(k + RBG) * px + i + RBG;
-        const T ue = i + 1 < nx ? T(0.5) * (u2[o] + u2[o + 1]) : T(0);
-        const T uw = i > 0 ? T(0.5) * (u2[o - 1] + u2[o]) : T(0);
-        const T wn = k + 1 < nz ? T(0.5) * (w2[o] + w2[o + px]) : T(0);
-        const T ws = k > 0 ? T(0.5) * (w2[o - px] + w2[o]) : T(0);
+        const T uc = u2(o), wc = w2(o);
+        o_u[o] = uc;
+        o_w[o] = wc;
+        store_mirrored(o_t, k, i, at[o] + dt * (w[o] + lap(th, o)), nx, nz, T(1), T(-1));
+        const T ue = i + 1 < nx ? T(0.5) * (uc + u2(o + 1)) : T(0);
+        const T uw = i > 0 ? T(0.5) * (u2(o - 1) + uc) : T(0);
+        const T wn = k + 1 < nz ? T(0.5) * (wc + w2(o + px)) : T(0);
+        const T ws = k > 0 ? T(0.5) * (w2(o - px) + wc) : T(0);
         d[c] = (ue - uw) * idx + (wn - ws) * idz;
     }
 }
 
-// C = op(A) op(B) for small dense row-major matrices (M x N result, inner K):
-// op(A)[m][k] = TA ? A[k][m] : A[m][k], same for B.  Tiles of 16 x 16.
-template <typename T, bool TA, bool TB>
-__global__ void k_rb_gemm(const T *A, const T *B, T *C, int M, int N, int K, int lda, int ldb, int ldc)
+// Forward transform and solve, one CTA per z mode k:
+//   R[i] = sum_m C_z[k][m] D[m][i],  F[k][j] = sum_i R[i] C_x[j][i] / lam_kj
+// (lam_kj = lz[k] + lx[j]; the constant mode F[0][0] = 0).  Every load is
+// coalesced across the threads or a broadcast (C_x enters transposed, cxT).
+template <typename T>
+__global__ void k_rb_forward(const T *D, const T *cz, const T *cxT, const T *lx, const T *lz, T *F, int nx, int nz)
 {
-    __shared__ T sa[16][17], sb[16][17];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int m = blockIdx.y * 16 + ty, nn = blockIdx.x * 16 + tx;
-    T acc = T(0);
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        const int ka = k0 + tx, kb = k0 + ty;
-        const int am = blockIdx.y * 16 + ty, bn = blockIdx.x * 16 + tx;
-        sa[ty][tx] = (am < M && ka < K) ? (TA ? A[(int64_t)ka * lda + am] : A[(int64_t)am * lda + ka]) : T(0);
-        sb[ty][tx] = (kb < K && bn < N) ? (TB ? B[(int64_t)bn * ldb + kb] : B[(int64_t)kb * ldb + bn]) : T(0);
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) acc += sa[ty][kk] * sb[kk][tx];
-        __syncthreads();
+    extern __shared__ __align__(16) unsigned char rb_smem[];
+    T *R = reinterpret_cast<T *>(rb_smem);
+    const int k = blockIdx.x;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        T a0 = T(0), a1 = T(0);
+        int m = 0;
+        for (; m + 1 < nz; m += 2) {
+            a0 += cz[(int64_t)k * nz + m] * D[(int64_t)m * nx + i];
+            a1 += cz[(int64_t)k * nz + m + 1] * D[(int64_t)(m + 1) * nx + i];
+        }
+        if (m < nz) a0 += cz[(int64_t)k * nz + m] * D[(int64_t)m * nx + i];
+        R[i] = a0 + a1;
     }
-    if (m < M && nn < N) C[(int64_t)m * ldc + nn] = acc;
+    __syncthreads();
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+        T a0 = T(0), a1 = T(0);
+        int i = 0;
+        for (; i + 1 < nx; i += 2) {
+            a0 += R[i] * cxT[(int64_t)i * nx + j];
+            a1 += R[i + 1] * cxT[(int64_t)(i + 1) * nx + j];
+        }
+        if (i < nx) a0 += R[i] * cxT[(int64_t)i * nx + j];
+        F[(int64_t)k * nx + j] = (k == 0 && j == 0) ? T(0) : (a0 + a1) / (lz[k] + lx[j]);
+    }
 }
 
-// F[k][j] /= (lz[k] + lx[j]); the constant mode is set to zero.
+// Inverse transform, one CTA per row m of phi:
+//   R[j] = sum_k C_z[k][m] F[k][j],  phi[m][i] = sum_j R[j] C_x[j][i].
 template <typename T>
-__global__ void k_rb_scale(T *F, const T *lx, const T *lz, int nx, int nz)
+__global__ void k_rb_inverse(const T *F, const T *cz, const T *cx, T *phi, int nx, int nz)
 {
-    const int n = nx * nz;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        const int k = c / nx, j = c - (c / nx) * nx;
-        F[c] = c == 0 ? T(0) : F[c] / (lz[k] + lx[j]);
+    extern __shared__ __align__(16) unsigned char rb_smem[];
+    T *R = reinterpret_cast<T *>(rb_smem);
+    const int m = blockIdx.x;
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+        T a0 = T(0), a1 = T(0);
+        int k = 0;
+        for (; k + 1 < nz; k += 2) {
+            a0 += cz[(int64_t)k * nz + m] * F[(int64_t)k * nx + j];
+            a1 += cz[(int64_t)(k + 1) * nz + m] * F[(int64_t)(k + 1) * nx + j];
+        }
+        if (k < nz) a0 += cz[(int64_t)k * nz + m] * F[(int64_t)k * nx + j];
+        R[j] = a0 + a1;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        T a0 = T(0), a1 = T(0);
+        int j = 0;
+        for (; j + 1 < nx; j += 2) {
+            a0 += R[j] * cx[(int64_t)j * nx + i];
+            a1 += R[j + 1] * cx[(int64_t)(j + 1) * nx + i];
+        }
+        if (j < nx) a0 += R[j] * cx[(int64_t)j * nx + i];
+        phi[(int64_t)m * nx + i] = a0 + a1;
     }
 }
 
 // Projection: cells take the average of their two faces' gradient corrections
 // (face gradient (phi_{i+1} - phi_i) / dx inside, zero on the walls); the
-// result is the new u, w (interior of the padded state).
+// result is the new u, w with their ghost images.
 template <typename T>
 __global__ void k_rb_project(const T *u2, const T *w2, const T *phi, T *u, T *w, int nx, int nz, T idx, T idz)
 {
-    const int px = nx + 2 * RBG;
+    const int px = rb_px(nx);
     const int n = nx * nz;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         const int k = c / nx, i = c - (c / nx) * nx;
@@ -144,8 +207,8 @@ __global__ void k_rb_project(const T *u2, const T *w2, const T *phi, T *u, T *w,
         const T gw = i > 0 ? (phi[c] - phi[c - 1]) * idx : T(0);
         const T gn = k + 1 < nz ? (phi[c + nx] - phi[c]) * idz : T(0);
         const T gs = k > 0 ? (phi[c] - phi[c - nx]) * idz : T(0);
-        u[o] = u2[o] - T(0.5) * (gw + ge);
-        w[o] = w2[o] - T(0.5) * (gs + gn);
+        store_mirrored(u, k, i, u2[o] - T(0.5) * (gw + ge), nx, nz, T(-1), T(-1));
+        store_mirrored(w, k, i, w2[o] - T(0.5) * (gs + gn), nx, nz, T(-1), T(-1));
     }
 }
 
@@ -153,7 +216,7 @@ __global__ void k_rb_project(const T *u2, const T *w2, const T *phi, T *u, T *w,
 template <typename T>
 __global__ void k_rb_copy(const T *src, T *dst, int nx, int nz, bool to_padded)
 {
-    const int px = nx + 2 * RBG;
+    const int px = rb_px(nx);
     const int n = nx * nz;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         const int k = c / nx, i = c - (c / nx) * nx;
@@ -166,6 +229,18 @@ __global__ void k_rb_copy(const T *src, T *dst, int nx, int nz, bool to_padded)
 }
 
 int blocks_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
+
+// Threads per CTA for the per-cell kernels: FP64 arithmetic is scarce per SM,
+// so small boxes spread over as many SMs as there are (152 on this part)
+// before CTAs grow.
+int cell_block(int64_t n)
+{
+    int b = 32;
+    while (b < 256 && (n + b - 1) / b > 4 * 152) b *= 2;
+    return b;
+}
+int cell_grid(int64_t n, int b) { return (int)std::min<int64_t>((n + b - 1) / b, 4096); }
+int row_block(int nx) { return std::min(256, (nx + 31) / 32 * 32); }
 
 }  // namespace
 }  // namespace sl
@@ -186,8 +261,15 @@ struct sl_rb {
     void *S[2] = {nullptr, nullptr}, *A = nullptr, *W = nullptr;
     // interior arrays: divergence / transform work, phi
     void *d = nullptr, *t1 = nullptr, *phi = nullptr;
-    void *cx = nullptr, *cz = nullptr, *lx = nullptr, *lz = nullptr;   // DCT matrices, eigenvalues
+    // orthonormal DCT-II matrices C_x (and its transpose), C_z; eigenvalues per axis
+    void *cx = nullptr, *cxT = nullptr, *cz = nullptr, *lx = nullptr, *lz = nullptr;
     int *signs = nullptr;   // sx of (u, w, theta), then sz of (u, w, theta)
+    // long runs replay kRbGraphSteps steps from one CUDA graph, captured for
+    // one dt and one starting buffer on a stream of the box's own
+    cudaStream_t cs = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double graph_dt = 0.0;
+    int graph_cur = -1;
 };
 
 namespace {
@@ -196,43 +278,38 @@ template <typename T>
 int rb_step_t(sl_rb *r, double dt, int nsteps, cudaStream_t st)
 {
     const int nx = r->nx, nz = r->nz, n = nx * nz;
-    const int px = nx + 2 * RBG, pz = nz + 2 * RBG;
+    const int px = rb_px(nx), pz = nz + 2 * RBG;
     const int64_t P = r->plane;
     T *A = static_cast<T *>(r->A), *Wk = static_cast<T *>(r->W);
-    T *d = static_cast<T *>(r->d), *t1 = static_cast<T *>(r->t1), *phi = static_cast<T *>(r->phi);
-    const T *cx = static_cast<const T *>(r->cx), *cz = static_cast<const T *>(r->cz);
+    T *d = static_cast<T *>(r->d), *F = static_cast<T *>(r->t1), *phi = static_cast<T *>(r->phi);
+    const T *cx = static_cast<const T *>(r->cx), *cxT = static_cast<const T *>(r->cxT);
+    const T *cz = static_cast<const T *>(r->cz);
     const T *lx = static_cast<const T *>(r->lx), *lz = static_cast<const T *>(r->lz);
     const double dx = r->Lx / nx, dz = r->Lz / nz;
     const int64_t pdims[3] = {px, pz, 1};
     const double sp[3] = {dx, dz, 1.0};
-    const int gb = blocks_for(P * 3), cb = blocks_for(n);
-    const dim3 gblk(16, 16);
-    auto grid2 = [](int M, int N) { return dim3((N + 15) / 16, (M + 15) / 16); };
+    const int cbk = cell_block(n), cgr = cell_grid(n, cbk), rbk = row_block(nx);
+    const size_t rsm = sizeof(T) * nx;
     for (int s = 0; s < nsteps; ++s) {
+        // S0 holds step n with its ghost layers (the walls' mirror images)
         T *S0 = static_cast<T *>(r->S[r->cur]), *S1 = static_cast<T *>(r->S[r->cur ^ 1]);
-        // the walls' mirror images in the ghost layers of u, w, theta
-        k_rb_ghosts<T><<<gb, 256, 0, st>>>(S0, 3, nx, nz, P, r->signs, r->signs + 3);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return set_error(SL_ERR_CUDA, cudaGetErrorString(e));
         // semi-Lagrangian advection of u, w, theta by U^n on the padded box;
         // CEC alternates its sweep order with the step index
         const void *ins[3] = {S0, S0 + P, S0 + 2 * P};
         void *outs[3] = {A, A + P, A + 2 * P};
         int rc = sl_advect_multi(outs, ins, 3, S0, 2, pdims, sp, dt, r->scheme, r->dtype, (int)(r->step & 1), st);
         if (rc) return rc;
-        // forces: u2, w2 into the work planes, theta' straight into the next state
-        k_rb_forces<T><<<cb, 256, 0, st>>>(S0, S0 + P, S0 + 2 * P, A, A + P, A + 2 * P, Wk, Wk + P, S1 + 2 * P, nx,
-                                           nz, T(dt), T(r->Ra), T(r->Pr), T(1.0 / (dx * dx)), T(1.0 / (dz * dz)));
-        k_rb_div<T><<<cb, 256, 0, st>>>(Wk, Wk + P, d, nx, nz, T(1.0 / dx), T(1.0 / dz));
+        // forces: u2, w2 into the work planes, theta' (with ghosts) into the
+        // next state, the face divergence D into d
+        k_rb_forces<T><<<cgr, cbk, 0, st>>>(S0, S0 + P, S0 + 2 * P, A, A + P, A + 2 * P, Wk, Wk + P, S1 + 2 * P, d, nx,
+                                            nz, T(dt), T(r->Ra), T(r->Pr), T(1.0 / (dx * dx)), T(1.0 / (dz * dz)),
+                                            T(1.0 / dx), T(1.0 / dz));
         // phi = C_z^T [(C_z D C_x^T) / lam] C_x
-        k_rb_gemm<T, false, false><<<grid2(nz, nx), gblk, 0, st>>>(cz, d, t1, nz, nx, nz, nz, nx, nx);
-        k_rb_gemm<T, false, true><<<grid2(nz, nx), gblk, 0, st>>>(t1, cx, d, nz, nx, nx, nx, nx, nx);
-        k_rb_scale<T><<<cb, 256, 0, st>>>(d, lx, lz, nx, nz);
-        k_rb_gemm<T, true, false><<<grid2(nz, nx), gblk, 0, st>>>(cz, d, t1, nz, nx, nz, nz, nx, nx);
-        k_rb_gemm<T, false, false><<<grid2(nz, nx), gblk, 0, st>>>(t1, cx, phi, nz, nx, nx, nx, nx, nx);
-        // the projected u, w of the next state
-        k_rb_project<T><<<cb, 256, 0, st>>>(Wk, Wk + P, phi, S1, S1 + P, nx, nz, T(1.0 / dx), T(1.0 / dz));
-        e = cudaGetLastError();
+        k_rb_forward<T><<<nz, rbk, rsm, st>>>(d, cz, cxT, lx, lz, F, nx, nz);
+        k_rb_inverse<T><<<nz, rbk, rsm, st>>>(F, cz, cx, phi, nx, nz);
+        // the projected u, w (with ghosts) of the next state
+        k_rb_project<T><<<cgr, cbk, 0, st>>>(Wk, Wk + P, phi, S1, S1 + P, nx, nz, T(1.0 / dx), T(1.0 / dz));
+        const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return set_error(SL_ERR_CUDA, cudaGetErrorString(e));
         r->cur ^= 1;
         ++r->step;
@@ -250,6 +327,7 @@ int rb_copy_t(sl_rb *r, const void *u, const void *w, const void *t, void *ou, v
         k_rb_copy<T><<<cb, 256, 0, st>>>(static_cast<const T *>(u), S, r->nx, r->nz, true);
         k_rb_copy<T><<<cb, 256, 0, st>>>(static_cast<const T *>(w), S + P, r->nx, r->nz, true);
         k_rb_copy<T><<<cb, 256, 0, st>>>(static_cast<const T *>(t), S + 2 * P, r->nx, r->nz, true);
+        k_rb_ghosts<T><<<blocks_for(3 * P), 256, 0, st>>>(S, 3, r->nx, r->nz, P, r->signs, r->signs + 3);
     } else {
         k_rb_copy<T><<<cb, 256, 0, st>>>(S, static_cast<T *>(ou), r->nx, r->nz, false);
         k_rb_copy<T><<<cb, 256, 0, st>>>(S + P, static_cast<T *>(ow), r->nx, r->nz, false);
@@ -257,6 +335,50 @@ int rb_copy_t(sl_rb *r, const void *u, const void *w, const void *t, void *ou, v
     }
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SL_OK : set_error(SL_ERR_CUDA, cudaGetErrorString(e));
+}
+
+constexpr int kRbGraphSteps = 8;   // even: the graph ends on the buffer and sweep order it starts on
+
+int rb_eager(sl_rb *r, double dt, int nsteps, cudaStream_t st)
+{
+    return r->dtype == SL_F64 ? rb_step_t<double>(r, dt, nsteps, st) : rb_step_t<float>(r, dt, nsteps, st);
+}
+
+// The graph of kRbGraphSteps steps from the current buffer with this dt
+// (captured again when either differs from the cached graph's).
+int rb_graph(sl_rb *r, double dt)
+{
+    if (r->exec && r->graph_dt == dt && r->graph_cur == r->cur) return SL_OK;
+    if (r->exec) {
+        cudaGraphExecDestroy(r->exec);
+        r->exec = nullptr;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!r->cs) e = cudaStreamCreateWithFlags(&r->cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return set_error(SL_ERR_CUDA, cudaGetErrorString(e));
+    const int cur0 = r->cur;
+    const int64_t step0 = r->step;
+    e = cudaStreamBeginCapture(r->cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return set_error(SL_ERR_CUDA, cudaGetErrorString(e));
+    const int rc = rb_eager(r, dt, kRbGraphSteps, r->cs);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(r->cs, &g);
+    r->cur = cur0;   // nothing ran yet
+    r->step = step0;
+    if (rc != SL_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc != SL_OK ? rc : set_error(SL_ERR_CUDA, cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&r->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        r->exec = nullptr;
+        return set_error(SL_ERR_CUDA, cudaGetErrorString(e));
+    }
+    r->graph_dt = dt;
+    r->graph_cur = cur0;
+    return SL_OK;
 }
 
 // orthonormal DCT-II matrix, row j: s_j cos(pi j (i + 1/2) / n)
@@ -298,10 +420,10 @@ int sl_rb_create(sl_rb **out, int nx, int nz, double Lx, double Lz, double Ra, d
     r->esz = dtype == SL_F64 ? 8 : 4;
     // the planes of one state are contiguous (the advection's velocity is
     // (u, w)); every buffer starts on a 512-byte boundary
-    r->plane = (int64_t)(nx + 2 * RBG) * (nz + 2 * RBG);
+    r->plane = (int64_t)rb_px(nx) * (nz + 2 * RBG);
     auto round64 = [](int64_t k) { return (k + 63) / 64 * 64; };
     const int64_t n = (int64_t)nx * nz;
-    const int64_t elems = 4 * round64(3 * r->plane) + 3 * round64(n) + round64((int64_t)nx * nx) +
+    const int64_t elems = 4 * round64(3 * r->plane) + 3 * round64(n) + 2 * round64((int64_t)nx * nx) +
                           round64((int64_t)nz * nz) + round64(nx) + round64(nz) + 64;
     if (cudaMalloc(&r->mem, r->esz * elems) != cudaSuccess) {
         delete r;
@@ -321,12 +443,15 @@ int sl_rb_create(sl_rb **out, int nx, int nz, double Lx, double Lz, double Ra, d
     r->t1 = take(n);
     r->phi = take(n);
     r->cx = take((int64_t)nx * nx);
+    r->cxT = take((int64_t)nx * nx);
     r->cz = take((int64_t)nz * nz);
     r->lx = take(nx);
     r->lz = take(nz);
     r->signs = reinterpret_cast<int *>(p);
-    std::vector<double> cxm, czm, lxv(nx), lzv(nz);
+    std::vector<double> cxm, czm, cxt((size_t)nx * nx), lxv(nx), lzv(nz);
     dct_matrix(cxm, nx);
+    for (int j = 0; j < nx; ++j)
+        for (int i = 0; i < nx; ++i) cxt[(size_t)i * nx + j] = cxm[(size_t)j * nx + i];
     dct_matrix(czm, nz);
     const double dx = Lx / nx, dz = Lz / nz;
     for (int j = 0; j < nx; ++j) lxv[j] = -4.0 / (dx * dx) * std::pow(std::sin(M_PI * j / (2.0 * nx)), 2);
@@ -343,6 +468,7 @@ int sl_rb_create(sl_rb **out, int nx, int nz, double Lx, double Lz, double Ra, d
         }
     };
     up(r->cx, cxm);
+    up(r->cxT, cxt);
     up(r->cz, czm);
     up(r->lx, lxv);
     up(r->lz, lzv);
@@ -379,12 +505,29 @@ int sl_rb_step(sl_rb *r, double dt, int nsteps, void *stream)
     DevCtx *c = ctx_get();
     if (!c || c->device != r->device) return set_error(SL_ERR_ARG, "the box belongs to another device");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    return r->dtype == SL_F64 ? rb_step_t<double>(r, dt, nsteps, st) : rb_step_t<float>(r, dt, nsteps, st);
+    int left = nsteps, rc = SL_OK;
+    if (left >= 2 * kRbGraphSteps) {
+        if (r->step & 1) {   // graphs start on an even step (CEC's x-first sweep)
+            rc = rb_eager(r, dt, 1, st);
+            if (rc) return rc;
+            --left;
+        }
+        rc = rb_graph(r, dt);
+        if (rc) return rc;
+        for (; left >= kRbGraphSteps; left -= kRbGraphSteps) {
+            const cudaError_t e = cudaGraphLaunch(r->exec, st);
+            if (e != cudaSuccess) return set_error(SL_ERR_CUDA, cudaGetErrorString(e));
+            r->step += kRbGraphSteps;
+        }
+    }
+    return left ? rb_eager(r, dt, left, st) : SL_OK;
 }
 
 int sl_rb_destroy(sl_rb *r)
 {
     if (!r) return SL_OK;
+    if (r->exec) cudaGraphExecDestroy(r->exec);
+    if (r->cs) cudaStreamDestroy(r->cs);
     if (r->mem) cudaFree(r->mem);
     delete r;
     return SL_OK;

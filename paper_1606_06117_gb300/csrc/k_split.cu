@@ -258,8 +258,11 @@ __device__ __forceinline__ void xyz_item(const Geo &g, int item, const T *__rest
 
 template <typename T, typename D, int TX, int TY, bool HAS_Z, bool VEC>
 __global__ void __launch_bounds__(XYZ<T, D, TX, TY, HAS_Z, VEC>::NT)
-k_cec_xyz(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ vel, Geo g)
+k_cec_xyz(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ vel, Geo g, int64_t fin,
+          int64_t fout)
 {
+    in += (int64_t)blockIdx.y * fin;   // field of this CTA (FieldSet)
+    out += (int64_t)blockIdx.y * fout;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nitems = g.tiles_x * g.tiles_y * g.chunks;
     bool bad = false;
@@ -427,8 +430,11 @@ __device__ __forceinline__ void zyx_item(const Geo &g, int item, const T *__rest
 
 template <typename T, typename D, int TX, int TY, bool HAS_Z, bool VEC>
 __global__ void __launch_bounds__(256)
-k_cec_zyx(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ vel, Geo g)
+k_cec_zyx(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ vel, Geo g, int64_t fin,
+          int64_t fout)
 {
+    in += (int64_t)blockIdx.y * fin;   // field of this CTA (FieldSet)
+    out += (int64_t)blockIdx.y * fout;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nitems = g.tiles_x * g.tiles_y * g.chunks;
     bool bad = false;
@@ -439,7 +445,7 @@ k_cec_zyx(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
 
 template <typename T, typename D, int TX, int TY, bool HAS_Z, bool VEC>
 cudaError_t dispatch_order(int parity, const Geo &g, int grid, const void *in, void *out, const void *vel,
-                           cudaStream_t st)
+                           const FieldSet &fs, cudaStream_t st)
 {
     const T *i = static_cast<const T *>(in);
     const T *v = static_cast<const T *>(vel);
@@ -451,7 +457,7 @@ cudaError_t dispatch_order(int parity, const Geo &g, int grid, const void *in, v
         if (e != cudaSuccess) return e;
         const int nitems = g.tiles_x * g.tiles_y * g.chunks;
         const int gr = grid > 0 && grid < nitems ? grid : nitems;
-        kern<<<gr, K::NT, K::smem(), st>>>(i, o, v, g);
+        kern<<<dim3(gr, fs.n), K::NT, K::smem(), st>>>(i, o, v, g, fs.fin, fs.fout);
     } else {
         using K = ZYX<T, D, TX, TY / 2, HAS_Z, VEC>;
         auto kern = k_cec_zyx<T, D, TX, TY / 2, HAS_Z, VEC>;
@@ -461,7 +467,7 @@ cudaError_t dispatch_order(int parity, const Geo &g, int grid, const void *in, v
         g2.tiles_y = (g.ny + TY / 2 - 1) / (TY / 2);
         const int nitems = g2.tiles_x * g2.tiles_y * g2.chunks;
         const int gr = grid > 0 && grid < nitems ? grid : nitems;
-        kern<<<gr, K::NT, K::smem(), st>>>(i, o, v, g2);
+        kern<<<dim3(gr, fs.n), K::NT, K::smem(), st>>>(i, o, v, g2, fs.fin, fs.fout);
     }
     return cudaGetLastError();
 }
@@ -517,7 +523,7 @@ int default_tz(int dtype, int ndim, const int64_t dims[3])
 
 cudaError_t launch_split_cec(int dtype, const void *in, void *out, const void *vel, int ndim,
                              const int64_t dims[3], const double s[3], int parity, Launch lc,
-                             unsigned *status, cudaStream_t st)
+                             unsigned *status, cudaStream_t st, FieldSet fs)
 {
     constexpr int TX = 32;
     Geo g;
@@ -540,26 +546,26 @@ cudaError_t launch_split_cec(int dtype, const void *in, void *out, const void *v
         g.tiles_y = (g.ny + TY - 1) / TY;
         const bool vec = lc.aligned && g.nx % 2 == 0;
         if (has_z)
-            return vec ? dispatch_order<double, double, TX, TY, true, true>(parity, g, lc.grid, in, out, vel, st)
-                       : dispatch_order<double, double, TX, TY, true, false>(parity, g, lc.grid, in, out, vel, st);
-        return vec ? dispatch_order<double, double, TX, TY, false, true>(parity, g, lc.grid, in, out, vel, st)
-                   : dispatch_order<double, double, TX, TY, false, false>(parity, g, lc.grid, in, out, vel, st);
+            return vec ? dispatch_order<double, double, TX, TY, true, true>(parity, g, lc.grid, in, out, vel, fs, st)
+                       : dispatch_order<double, double, TX, TY, true, false>(parity, g, lc.grid, in, out, vel, fs, st);
+        return vec ? dispatch_order<double, double, TX, TY, false, true>(parity, g, lc.grid, in, out, vel, fs, st)
+                   : dispatch_order<double, double, TX, TY, false, false>(parity, g, lc.grid, in, out, vel, fs, st);
     }
     constexpr int TY = 32;
     g.tiles_y = (g.ny + TY - 1) / TY;
     const bool vec = lc.aligned && g.nx % 4 == 0;
     if (dtype == 2) {   // SL_F32_D64
         if (has_z)
-            return vec ? dispatch_order<float, double, TX, TY, true, true>(parity, g, lc.grid, in, out, vel, st)
-                       : dispatch_order<float, double, TX, TY, true, false>(parity, g, lc.grid, in, out, vel, st);
-        return vec ? dispatch_order<float, double, TX, TY, false, true>(parity, g, lc.grid, in, out, vel, st)
-                   : dispatch_order<float, double, TX, TY, false, false>(parity, g, lc.grid, in, out, vel, st);
+            return vec ? dispatch_order<float, double, TX, TY, true, true>(parity, g, lc.grid, in, out, vel, fs, st)
+                       : dispatch_order<float, double, TX, TY, true, false>(parity, g, lc.grid, in, out, vel, fs, st);
+        return vec ? dispatch_order<float, double, TX, TY, false, true>(parity, g, lc.grid, in, out, vel, fs, st)
+                   : dispatch_order<float, double, TX, TY, false, false>(parity, g, lc.grid, in, out, vel, fs, st);
     }
     if (has_z)
-        return vec ? dispatch_order<float, float, TX, TY, true, true>(parity, g, lc.grid, in, out, vel, st)
-                   : dispatch_order<float, float, TX, TY, true, false>(parity, g, lc.grid, in, out, vel, st);
-    return vec ? dispatch_order<float, float, TX, TY, false, true>(parity, g, lc.grid, in, out, vel, st)
-               : dispatch_order<float, float, TX, TY, false, false>(parity, g, lc.grid, in, out, vel, st);
+        return vec ? dispatch_order<float, float, TX, TY, true, true>(parity, g, lc.grid, in, out, vel, fs, st)
+                   : dispatch_order<float, float, TX, TY, true, false>(parity, g, lc.grid, in, out, vel, fs, st);
+    return vec ? dispatch_order<float, float, TX, TY, false, true>(parity, g, lc.grid, in, out, vel, fs, st)
+               : dispatch_order<float, float, TX, TY, false, false>(parity, g, lc.grid, in, out, vel, fs, st);
 }
 
 size_t batched_smem(int parity)

@@ -136,8 +136,10 @@ struct RowChunks {
 
 template <typename T, typename D, int NST, int TX, int TY, bool HAS_Z, bool VEC>
 __global__ void __launch_bounds__(256)
-k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ vel, Geo g)
+k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ vel, Geo g, int64_t fin, int64_t fout)
 {
+    in += (int64_t)blockIdx.y * fin;   // field of this CTA (FieldSet)
+    out += (int64_t)blockIdx.y * fout;
     using K = Cfg<T, D, NST, TX, TY, HAS_Z>;
     constexpr int NT = K::NT, H = K::H, PW = K::PW, SLOT = K::SLOT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -314,7 +316,7 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
 }
 
 template <typename T, typename D, int NST, int TX, int TY, bool HAS_Z, bool VEC>
-cudaError_t go(Geo g, int grid, const void *in, void *out, const void *vel, cudaStream_t st)
+cudaError_t go(Geo g, int grid, const void *in, void *out, const void *vel, const FieldSet &fs, cudaStream_t st)
 {
     using K = Cfg<T, D, NST, TX, TY, HAS_Z>;
     auto kern = k_unsplit<T, D, NST, TX, TY, HAS_Z, VEC>;
@@ -339,39 +341,49 @@ cudaError_t go(Geo g, int grid, const void *in, void *out, const void *vel, cuda
     const int64_t total = (int64_t)g.tiles_x * g.tiles_y * (persist ? g.nz : g.chunks);
     int gr = grid > 0 ? grid : (persist ? per_dev[dev] : (int)total);
     if (gr > total) gr = (int)total;
-    kern<<<gr, K::NT, K::smem(), st>>>(static_cast<const T *>(in), static_cast<T *>(out),
-                                       static_cast<const T *>(vel), g);
+    kern<<<dim3(gr, fs.n), K::NT, K::smem(), st>>>(static_cast<const T *>(in), static_cast<T *>(out),
+                                                   static_cast<const T *>(vel), g, fs.fin, fs.fout);
     return cudaGetLastError();
 }
 
 template <typename T, typename D, int TY, bool HAS_Z, bool VEC>
-cudaError_t by_scheme(int scheme, const Geo &g, int grid, const void *in, void *out, const void *vel, cudaStream_t st)
+cudaError_t by_scheme(int scheme, const Geo &g, int grid, const void *in, void *out, const void *vel,
+                      const FieldSet &fs, cudaStream_t st)
 {
     switch (scheme) {
-    case 0: return go<T, D, 1, 32, TY, HAS_Z, VEC>(g, grid, in, out, vel, st);
-    case 1: return go<T, D, 2, 32, TY, HAS_Z, VEC>(g, grid, in, out, vel, st);
-    default: return go<T, D, 3, 32, TY, HAS_Z, VEC>(g, grid, in, out, vel, st);
+    case 0: return go<T, D, 1, 32, TY, HAS_Z, VEC>(g, grid, in, out, vel, fs, st);
+    case 1: return go<T, D, 2, 32, TY, HAS_Z, VEC>(g, grid, in, out, vel, fs, st);
+    default: return go<T, D, 3, 32, TY, HAS_Z, VEC>(g, grid, in, out, vel, fs, st);
     }
 }
 
 template <typename T, typename D, int TY>
 cudaError_t by_shape(int scheme, bool has_z, bool vec, const Geo &g, int grid, const void *in, void *out,
-                     const void *vel, cudaStream_t st)
+                     const void *vel, const FieldSet &fs, cudaStream_t st)
 {
     if (has_z)
-        return vec ? by_scheme<T, D, TY, true, true>(scheme, g, grid, in, out, vel, st)
-                   : by_scheme<T, D, TY, true, false>(scheme, g, grid, in, out, vel, st);
-    return vec ? by_scheme<T, D, TY, false, true>(scheme, g, grid, in, out, vel, st)
-               : by_scheme<T, D, TY, false, false>(scheme, g, grid, in, out, vel, st);
+        return vec ? by_scheme<T, D, TY, true, true>(scheme, g, grid, in, out, vel, fs, st)
+                   : by_scheme<T, D, TY, true, false>(scheme, g, grid, in, out, vel, fs, st);
+    return vec ? by_scheme<T, D, TY, false, true>(scheme, g, grid, in, out, vel, fs, st)
+               : by_scheme<T, D, TY, false, false>(scheme, g, grid, in, out, vel, fs, st);
 }
 
 }  // namespace
 
 cudaError_t launch_unsplit(int dtype, int scheme, const void *in, void *out, const void *vel, int ndim,
-                           const int64_t dims[3], const double s[3], Launch lc, unsigned *status, cudaStream_t st)
+                           const int64_t dims[3], const double s[3], Launch lc, unsigned *status, cudaStream_t st,
+                           FieldSet fs)
 {
-    if (scheme == 0 && cir_fast_eligible(dtype, ndim, dims, lc.aligned))
-        return launch_cir_fast(in, out, vel, dims, s, lc, status, st);
+    if (scheme == 0 && cir_fast_eligible(dtype, ndim, dims, lc.aligned)) {
+        const size_t es = dtype == 1 ? 8 : 4;
+        for (int f = 0; f < fs.n; ++f) {
+            const cudaError_t e = launch_cir_fast(static_cast<const char *>(in) + f * fs.fin * es,
+                                                  static_cast<char *>(out) + f * fs.fout * es, vel, dims, s, lc,
+                                                  status, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     Geo g;
     g.nx = (int)dims[0];
     g.ny = (int)dims[1];
@@ -387,14 +399,14 @@ cudaError_t launch_unsplit(int dtype, int scheme, const void *in, void *out, con
     g.chunks = (g.nz + g.tz - 1) / g.tz;
     g.tiles_x = (g.nx + 31) / 32;
     const bool has_z = ndim == 3;
-    if (dtype == 1) return by_shape<double, double, 8>(scheme, has_z, lc.aligned && g.nx % 2 == 0, g, lc.grid, in, out, vel, st);
-    if (dtype == 2) return by_shape<float, double, 16>(scheme, has_z, lc.aligned && g.nx % 4 == 0, g, lc.grid, in, out, vel, st);
+    if (dtype == 1) return by_shape<double, double, 8>(scheme, has_z, lc.aligned && g.nx % 2 == 0, g, lc.grid, in, out, vel, fs, st);
+    if (dtype == 2) return by_shape<float, double, 16>(scheme, has_z, lc.aligned && g.nx % 4 == 0, g, lc.grid, in, out, vel, fs, st);
     const bool vec = lc.aligned && g.nx % 4 == 0;
     // FP32 3D grids with vector staging: tile heights 8 and 32 besides 16 (a
     // launch-shape choice; a cell's arithmetic does not depend on it)
-    if (has_z && vec && lc.ty == 8) return by_scheme<float, float, 8, true, true>(scheme, g, lc.grid, in, out, vel, st);
-    if (has_z && vec && lc.ty == 32) return by_scheme<float, float, 32, true, true>(scheme, g, lc.grid, in, out, vel, st);
-    return by_shape<float, float, 16>(scheme, has_z, vec, g, lc.grid, in, out, vel, st);
+    if (has_z && vec && lc.ty == 8) return by_scheme<float, float, 8, true, true>(scheme, g, lc.grid, in, out, vel, fs, st);
+    if (has_z && vec && lc.ty == 32) return by_scheme<float, float, 32, true, true>(scheme, g, lc.grid, in, out, vel, fs, st);
+    return by_shape<float, float, 16>(scheme, has_z, vec, g, lc.grid, in, out, vel, fs, st);
 }
 
 }  // namespace sl

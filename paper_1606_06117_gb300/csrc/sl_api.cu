@@ -176,15 +176,16 @@ Launch launch_for(int fam, const int64_t dims[3], int scheme, int dtype, bool al
 
 cudaError_t launch_family(int fam, const Launch &lc, void *out, const void *in, const void *vel, int ndim,
                           const int64_t dims[3], const double s[3], int scheme, int dtype, int parity,
-                          cudaStream_t st, DevCtx *c)
+                          cudaStream_t st, DevCtx *c, FieldSet fs = FieldSet())
 {
     if (fam == SL_KERNEL_CEC_FAST) {
         FastInst one;
         fast_fill(one, in, out, vel, dims, s, 0);
         return launch_cec_fast(one, nullptr, 1, (int64_t)one.ntiles * one.nz, parity, c->status, lc.grid, st);
     }
-    if (fam == SL_KERNEL_CEC_SPLIT) return launch_split_cec(dtype, in, out, vel, ndim, dims, s, parity, lc, c->status, st);
-    return launch_unsplit(dtype, scheme, in, out, vel, ndim, dims, s, lc, c->status, st);
+    if (fam == SL_KERNEL_CEC_SPLIT)
+        return launch_split_cec(dtype, in, out, vel, ndim, dims, s, parity, lc, c->status, st, fs);
+    return launch_unsplit(dtype, scheme, in, out, vel, ndim, dims, s, lc, c->status, st, fs);
 }
 
 int launch_step(void *out, const void *in, const void *vel, int ndim, const int64_t dims[3], const double s[3],
@@ -315,6 +316,33 @@ int sl_advect_multi(void *const *outs, const void *const *ins, int nfields, cons
             if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         }
         return SL_OK;
+    }
+    // fields at uniform strides that share one alignment: one launch whose
+    // CTAs of field f do what a launch for field f alone does
+    const ptrdiff_t es = (ptrdiff_t)elem_size(dtype);
+    const char *i0 = static_cast<const char *>(ins[0]), *o0 = static_cast<const char *>(outs[0]);
+    const bool al0 = aligned16(ins[0]) && aligned16(outs[0]);
+    const ptrdiff_t din = nfields > 1 ? static_cast<const char *>(ins[1]) - i0 : 0;
+    const ptrdiff_t dout = nfields > 1 ? static_cast<const char *>(outs[1]) - o0 : 0;
+    bool uniform = nfields > 1 && nfields <= 65535 && din % es == 0 && dout % es == 0;
+    for (int f = 0; f < nfields && uniform; ++f)
+        uniform = static_cast<const char *>(ins[f]) - i0 == f * din &&
+                  static_cast<const char *>(outs[f]) - o0 == f * dout &&
+                  (aligned16(ins[f]) && aligned16(outs[f])) == al0;
+    if (uniform) {
+        const bool al = al0 && aligned16(vel);
+        const int fam = family_of(scheme, dtype, ndim, dims, al);
+        if (fam != SL_KERNEL_CEC_FAST) {
+            const Launch lc = launch_for(fam, dims, scheme, dtype, al, c);
+            FieldSet fs;
+            fs.n = nfields;
+            fs.fin = din / es;
+            fs.fout = dout / es;
+            const cudaError_t e = launch_family(fam, lc, outs[0], ins[0], vel, ndim, dims, s, scheme, dtype,
+                                                step_parity, st, c, fs);
+            if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+            return SL_OK;
+        }
     }
     for (int f = 0; f < nfields; ++f) {
         rc = launch_step(outs[f], ins[f], vel, ndim, dims, s, scheme, dtype, step_parity, st, c);

@@ -30,13 +30,22 @@ struct Launch {
     bool aligned = true; // all base pointers 16-byte aligned (vector staging allowed)
 };
 
+// Several fields advected by one velocity in one launch: field f reads
+// in + f * fin and writes out + f * fout (elements); the launch's grid gains
+// a y extent of n, and each field's CTAs do exactly what a launch for that
+// field alone does.
+struct FieldSet {
+    int n = 1;
+    int64_t fin = 0, fout = 0;
+};
+
 // Fused single-step kernels; return a cudaError_t of the launch.
 cudaError_t launch_split_cec(int dtype, const void *in, void *out, const void *vel, int ndim,
                              const int64_t dims[3], const double s[3], int parity,
-                             Launch lc, unsigned *status, cudaStream_t st);
+                             Launch lc, unsigned *status, cudaStream_t st, FieldSet fs = FieldSet());
 cudaError_t launch_unsplit(int dtype, int scheme, const void *in, void *out, const void *vel,
                            int ndim, const int64_t dims[3], const double s[3], Launch lc,
-                           unsigned *status, cudaStream_t st);
+                           unsigned *status, cudaStream_t st, FieldSet fs = FieldSet());
 // FP32 3D CIR kernel on four-cell groups (k_cir_fast.cu); launch_unsplit routes
 // eligible CIR steps to it.
 bool cir_fast_eligible(int dtype, int ndim, const int64_t dims[3], bool aligned);
