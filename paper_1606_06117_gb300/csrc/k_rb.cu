@@ -128,68 +128,66 @@ __global__ void k_rb_forces(const T *u, const T *w, const T *th, const T *au, co
     }
 }
 
+// out(c) = sum_{t < K} a[t * as] B[t * ldb + c] for c < N, by the CTA's 256
+// threads: 64 columns at a time, each column's sum split over four thread
+// groups (t = g mod 4, two terms in flight per group) and combined in fixed
+// order in shared memory (part, 256 elements).
+template <typename T, typename Store>
+__device__ __forceinline__ void rb_vecmat(const T *a, int64_t as, const T *B, int64_t ldb, int K, int N, T *part,
+                                          Store store)
+{
+    const int c = threadIdx.x & 63, g = threadIdx.x >> 6;
+    for (int c0 = 0; c0 < N; c0 += 64) {
+        const int col = c0 + c;
+        T acc0 = T(0), acc1 = T(0);
+        if (col < N) {
+            int t = g;
+#pragma unroll 4
+            for (; t + 4 < K; t += 8) {
+                acc0 += a[t * as] * B[t * ldb + col];
+                acc1 += a[(t + 4) * as] * B[(t + 4) * ldb + col];
+            }
+            if (t < K) acc0 += a[t * as] * B[t * ldb + col];
+        }
+        part[g * 64 + c] = acc0 + acc1;
+        __syncthreads();
+        if (g == 0 && col < N) store(col, (part[c] + part[64 + c]) + (part[128 + c] + part[192 + c]));
+        __syncthreads();
+    }
+}
+
+constexpr int kRbRowThreads = 256;
+
 // Forward transform and solve, one CTA per z mode k:
 //   R[i] = sum_m C_z[k][m] D[m][i],  F[k][j] = sum_i R[i] C_x[j][i] / lam_kj
 // (lam_kj = lz[k] + lx[j]; the constant mode F[0][0] = 0).  Every load is
 // coalesced across the threads or a broadcast (C_x enters transposed, cxT).
 template <typename T>
-__global__ void k_rb_forward(const T *D, const T *cz, const T *cxT, const T *lx, const T *lz, T *F, int nx, int nz)
+__global__ void __launch_bounds__(kRbRowThreads)
+k_rb_forward(const T *D, const T *cz, const T *cxT, const T *lx, const T *lz, T *F, int nx, int nz)
 {
     extern __shared__ __align__(16) unsigned char rb_smem[];
-    T *R = reinterpret_cast<T *>(rb_smem);
+    T *part = reinterpret_cast<T *>(rb_smem), *R = part + kRbRowThreads;
     const int k = blockIdx.x;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        T a0 = T(0), a1 = T(0);
-        int m = 0;
-        for (; m + 1 < nz; m += 2) {
-            a0 += cz[(int64_t)k * nz + m] * D[(int64_t)m * nx + i];
-            a1 += cz[(int64_t)k * nz + m + 1] * D[(int64_t)(m + 1) * nx + i];
-        }
-        if (m < nz) a0 += cz[(int64_t)k * nz + m] * D[(int64_t)m * nx + i];
-        R[i] = a0 + a1;
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
-        T a0 = T(0), a1 = T(0);
-        int i = 0;
-        for (; i + 1 < nx; i += 2) {
-            a0 += R[i] * cxT[(int64_t)i * nx + j];
-            a1 += R[i + 1] * cxT[(int64_t)(i + 1) * nx + j];
-        }
-        if (i < nx) a0 += R[i] * cxT[(int64_t)i * nx + j];
-        F[(int64_t)k * nx + j] = (k == 0 && j == 0) ? T(0) : (a0 + a1) / (lz[k] + lx[j]);
-    }
+    rb_vecmat(cz + (int64_t)k * nz, 1, D, nx, nz, nx, part, [&](int i, T v) { R[i] = v; });
+    T *Fk = F + (int64_t)k * nx;
+    const T lk = lz[k];
+    rb_vecmat(R, 1, cxT, nx, nx, nx, part,
+              [&](int j, T v) { Fk[j] = (k == 0 && j == 0) ? T(0) : v / (lk + lx[j]); });
 }
 
 // Inverse transform, one CTA per row m of phi:
 //   R[j] = sum_k C_z[k][m] F[k][j],  phi[m][i] = sum_j R[j] C_x[j][i].
 template <typename T>
-__global__ void k_rb_inverse(const T *F, const T *cz, const T *cx, T *phi, int nx, int nz)
+__global__ void __launch_bounds__(kRbRowThreads)
+k_rb_inverse(const T *F, const T *cz, const T *cx, T *phi, int nx, int nz)
 {
     extern __shared__ __align__(16) unsigned char rb_smem[];
-    T *R = reinterpret_cast<T *>(rb_smem);
+    T *part = reinterpret_cast<T *>(rb_smem), *R = part + kRbRowThreads;
     const int m = blockIdx.x;
-    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
-        T a0 = T(0), a1 = T(0);
-        int k = 0;
-        for (; k + 1 < nz; k += 2) {
-            a0 += cz[(int64_t)k * nz + m] * F[(int64_t)k * nx + j];
-            a1 += cz[(int64_t)(k + 1) * nz + m] * F[(int64_t)(k + 1) * nx + j];
-        }
-        if (k < nz) a0 += cz[(int64_t)k * nz + m] * F[(int64_t)k * nx + j];
-        R[j] = a0 + a1;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        T a0 = T(0), a1 = T(0);
-        int j = 0;
-        for (; j + 1 < nx; j += 2) {
-            a0 += R[j] * cx[(int64_t)j * nx + i];
-            a1 += R[j + 1] * cx[(int64_t)(j + 1) * nx + i];
-        }
-        if (j < nx) a0 += R[j] * cx[(int64_t)j * nx + i];
-        phi[(int64_t)m * nx + i] = a0 + a1;
-    }
+    rb_vecmat(cz + m, nz, F, nx, nz, nx, part, [&](int j, T v) { R[j] = v; });
+    T *pm = phi + (int64_t)m * nx;
+    rb_vecmat(R, 1, cx, nx, nx, nx, part, [&](int i, T v) { pm[i] = v; });
 }
 
 // Projection: cells take the average of their two faces' gradient corrections
@@ -240,7 +238,7 @@ int cell_block(int64_t n)
     return b;
 }
 int cell_grid(int64_t n, int b) { return (int)std::min<int64_t>((n + b - 1) / b, 4096); }
-int row_block(int nx) { return std::min(256, (nx + 31) / 32 * 32); }
+
 
 }  // namespace
 }  // namespace sl
@@ -288,8 +286,8 @@ int rb_step_t(sl_rb *r, double dt, int nsteps, cudaStream_t st)
     const double dx = r->Lx / nx, dz = r->Lz / nz;
     const int64_t pdims[3] = {px, pz, 1};
     const double sp[3] = {dx, dz, 1.0};
-    const int cbk = cell_block(n), cgr = cell_grid(n, cbk), rbk = row_block(nx);
-    const size_t rsm = sizeof(T) * nx;
+    const int cbk = cell_block(n), cgr = cell_grid(n, cbk);
+    const size_t rsm = sizeof(T) * (kRbRowThreads + nx);
     for (int s = 0; s < nsteps; ++s) {
         // S0 holds step n with its ghost layers (the walls' mirror images)
         T *S0 = static_cast<T *>(r->S[r->cur]), *S1 = static_cast<T *>(r->S[r->cur ^ 1]);
@@ -305,8 +303,8 @@ int rb_step_t(sl_rb *r, double dt, int nsteps, cudaStream_t st)
                                             nz, T(dt), T(r->Ra), T(r->Pr), T(1.0 / (dx * dx)), T(1.0 / (dz * dz)),
                                             T(1.0 / dx), T(1.0 / dz));
         // phi = C_z^T [(C_z D C_x^T) / lam] C_x
-        k_rb_forward<T><<<nz, rbk, rsm, st>>>(d, cz, cxT, lx, lz, F, nx, nz);
-        k_rb_inverse<T><<<nz, rbk, rsm, st>>>(F, cz, cx, phi, nx, nz);
+        k_rb_forward<T><<<nz, kRbRowThreads, rsm, st>>>(d, cz, cxT, lx, lz, F, nx, nz);
+        k_rb_inverse<T><<<nz, kRbRowThreads, rsm, st>>>(F, cz, cx, phi, nx, nz);
         // the projected u, w (with ghosts) of the next state
         k_rb_project<T><<<cgr, cbk, 0, st>>>(Wk, Wk + P, phi, S1, S1 + P, nx, nz, T(1.0 / dx), T(1.0 / dz));
         const cudaError_t e = cudaGetLastError();
