@@ -29,8 +29,8 @@
 // itself (no separate fill pass), the forces kernel also gives the divergence,
 // the transforms run one CTA per mode row with coalesced or broadcast loads,
 // the per-cell kernels use small CTAs, and long runs replay the step from a
-// CUDA graph (7 launches per step: 3 advections, forces, two transforms,
-// projection).
+// CUDA graph (5 launches per step: the advection of the three fields in one
+// launch, forces, two transforms, projection).
 #include <cmath>
 #include <new>
 #include <vector>
