@@ -237,13 +237,19 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
                 constexpr int RW = TX + 2 * h, RH = TY + 2 * h;
                 const T *phi0 = sl_phi(q);
                 const T *cP = sl_c(q);
-                for (int r = tid; r < RW * RH; r += NT) {
-                    const int yy = r / RW, xx = r - (r / RW) * RW;
+                const T *phim = HAS_Z ? sl_phi(q - 1) : phi0, *php = HAS_Z ? sl_phi(q + 1) : phi0;
+                D *const lq = sl_l(q);
+                int yy = tid / RW, xx = tid - (tid / RW) * RW;
+                for (int r = tid; r < RW * RH; r += NT, xx += NT % RW, yy += NT / RW) {
+                    if (xx >= RW) {
+                        xx -= RW;
+                        ++yy;
+                    }
                     const int o = (yy - h + H) * PW + (xx - h + 4);
                     const D cx = D(cP[o]) * sxd, cy = D(cP[SC + o]) * syd;
                     const D cz = HAS_Z ? D(cP[2 * SC + o]) * szd : D(0);
                     const int ox = by_sign(cx, -1, 1, 0), oy = by_sign(cy, -PW, PW, 0);
-                    const T *phi1 = HAS_Z ? by_sign<D, const T *>(cz, sl_phi(q - 1), sl_phi(q + 1), phi0) : phi0;
+                    const T *phi1 = HAS_Z ? by_sign<D, const T *>(cz, phim, php, phi0) : phi0;
                     const D v = mlerp<D, HAS_Z>(phi0, phi1, o, ox, oy, D(1) - fabs(cx), D(1) - fabs(cy),
                                                 D(1) - fabs(cz));
                     if constexpr (NST == 1) {
@@ -251,7 +257,7 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
                         const int gx = x0 + xx, gy = y0 + yy;
                         if (gx < g.nx && gy < g.ny) out[(int64_t)(q >= g.nz ? q - g.nz : q) * g.plane + (int64_t)gy * g.nx + gx] = T(v);
                     } else {
-                        sl_l(q)[o] = v;
+                        lq[o] = v;
                     }
                 }
             }
@@ -265,14 +271,20 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
                     const T *phiq = sl_phi(q);
                     const T *cP = sl_c(q);
                     const D *l0 = sl_l(q);
-                    for (int r = tid; r < RW * RH; r += NT) {
-                        const int yy = r / RW, xx = r - (r / RW) * RW;
+                    const D *lp = HAS_Z ? sl_l(q + 1) : l0, *lm = HAS_Z ? sl_l(q - 1) : l0;
+                    T *const pq = sl_p(q);
+                    int yy = tid / RW, xx = tid - (tid / RW) * RW;
+                    for (int r = tid; r < RW * RH; r += NT, xx += NT % RW, yy += NT / RW) {
+                        if (xx >= RW) {
+                            xx -= RW;
+                            ++yy;
+                        }
                         const int o = (yy - h + H) * PW + (xx - h + 4);
                         const D cx = D(cP[o]) * sxd, cy = D(cP[SC + o]) * syd;
                         const D cz = HAS_Z ? D(cP[2 * SC + o]) * szd : D(0);
                         // reversed flow: departure x + u dt, corners toward +s
                         const int ox = by_sign(cx, 1, -1, 0), oy = by_sign(cy, PW, -PW, 0);
-                        const D *l1 = HAS_Z ? by_sign<D, const D *>(cz, sl_l(q + 1), sl_l(q - 1), l0) : l0;
+                        const D *l1 = HAS_Z ? by_sign<D, const D *>(cz, lp, lm, l0) : l0;
                         const D bar = mlerp<D, HAS_Z>(l0, l1, o, ox, oy, D(1) - fabs(cx), D(1) - fabs(cy),
                                                       D(1) - fabs(cz));
                         const D delta = D(phiq[o]) - bar;
@@ -282,7 +294,7 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
                             if (gx < g.nx && gy < g.ny)
                                 out[(int64_t)(q >= g.nz ? q - g.nz : q) * g.plane + (int64_t)gy * g.nx + gx] = T(l0[o] + delta * D(0.5));
                         } else {
-                            sl_p(q)[o] = T(D(phiq[o]) + delta * D(0.5));
+                            pq[o] = T(D(phiq[o]) + delta * D(0.5));
                         }
                     }
                 }
@@ -294,6 +306,7 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
                     const int q = HAS_Z ? p - 3 : 0;
                     const T *cP = sl_c(q);
                     const T *p0 = sl_p(q);
+                    const T *pm = HAS_Z ? sl_p(q - 1) : p0, *pp = HAS_Z ? sl_p(q + 1) : p0;
                     for (int r = tid; r < TX * TY; r += NT) {
                         const int yy = r / TX, xx = r - (r / TX) * TX;
                         const int o = (yy + H) * PW + (xx + 4);
@@ -301,7 +314,7 @@ k_unsplit(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ v
                         const T cz = HAS_Z ? T(D(cP[2 * SC + o]) * szd) : T(0);
                         bad |= fabs(cx) > T(1) || fabs(cy) > T(1) || fabs(cz) > T(1);
                         const int ox = by_sign(cx, -1, 1, 0), oy = by_sign(cy, -PW, PW, 0);
-                        const T *p1 = HAS_Z ? by_sign<T, const T *>(cz, sl_p(q - 1), sl_p(q + 1), p0) : p0;
+                        const T *p1 = HAS_Z ? by_sign<T, const T *>(cz, pm, pp, p0) : p0;
                         const T v = mlerp<T, HAS_Z>(p0, p1, o, ox, oy, T(1) - fabs(cx), T(1) - fabs(cy),
                                                     T(1) - fabs(cz));
                         const int gx = x0 + xx, gy = y0 + yy;
