@@ -176,12 +176,13 @@ def test_multi_field_launch_equals_single_calls(nfields, parity):
 
 @pytest.mark.parametrize("dtype", ["f32", "f64", "f32_d64"])
 @pytest.mark.parametrize("scheme", SCHEMES)
-@pytest.mark.parametrize("shape", [(6, 20, 36), (1, 42, 56)])
+@pytest.mark.parametrize("shape", [(6, 20, 36), (1, 42, 56), (8, 16, 64)])
 def test_strided_fields_share_one_launch_and_equal_single_calls(shape, scheme, dtype):
     """Fields stored back to back (uniform strides, one alignment) go through
-    the generic kernels in one launch with a field index per CTA row; every
-    field equals its single-field step bit for bit, the first matches the
-    oracle.  Fields at an odd FP32 plane size have mixed 16-byte alignment and
+    the generic kernels in one launch with a field index per CTA row (the
+    four-cell CIR kernel, which (8, 16, 64) in FP32 reaches, takes them one
+    launch each); every field equals its single-field step bit for bit, the
+    first matches the oracle.  Fields at an odd FP32 plane size have mixed 16-byte alignment and
     take one launch each; the results are the same."""
     nd = 2 if shape[0] == 1 else 3
     shp = shape[1:] if nd == 2 else shape
