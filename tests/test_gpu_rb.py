@@ -49,12 +49,12 @@ def random_start(nx, nz, seed, cmax, dt, Lx=2.0, Lz=1.0):
     return u, w, 0.1 * rng.standard_normal((nz, nx))
 
 
-def run_both(nx, nz, scheme, start, dt, steps, Ra, dtype=torch.float64):
-    box = R.Box(nx, nz, Ra=Ra, scheme=scheme)
+def run_both(nx, nz, scheme, start, dt, steps, Ra, dtype=torch.float64, Pr=1.0):
+    box = R.Box(nx, nz, Ra=Ra, Pr=Pr, scheme=scheme)
     box.u, box.w, box.theta = (np.array(a, dtype=np.float64) for a in start)
     if dtype == torch.float32:   # the oracle starts from the values the GPU receives
         box.u, box.w, box.theta = (a.astype(np.float32).astype(np.float64) for a in (box.u, box.w, box.theta))
-    g = sl.RayleighBenard(nx, nz, Ra=Ra, scheme=scheme, dtype=dtype)
+    g = sl.RayleighBenard(nx, nz, Ra=Ra, Pr=Pr, scheme=scheme, dtype=dtype)
     try:
         sl.sl_device_status()
         g.set_state(*(torch.from_numpy(np.ascontiguousarray(a)) for a in start))
@@ -102,7 +102,19 @@ def test_random_high_courant_steps_match_the_oracle(scheme, nx, nz):
         assert_parity(a, b, "f64", f"{scheme} {nx}x{nz} {name}", allowance(nx, nz, 2))
 
 
-@pytest.mark.parametrize("scheme", ["CIR", "CEC"])
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("Pr", [0.7, 4.0])
+def test_prandtl_numbers_other_than_one_match_the_oracle(scheme, Pr):
+    """Pr multiplies both the buoyancy and the viscous term (eq. e:nsnd); a
+    random start exercises both from the first step."""
+    nx, nz, dt = 24, 12, 2e-5
+    u, w, th = random_start(nx, nz, seed=7, cmax=0.2, dt=dt)
+    got, ref = run_both(nx, nz, scheme, (u, w, th), dt, 4, Ra=3e4, Pr=Pr)
+    for name, a, b in zip(("u", "w", "theta"), got, ref):
+        assert_parity(a, b, "f64", f"{scheme} Pr {Pr} {name}", allowance(nx, nz, 4))
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
 def test_float32_box_tracks_the_oracle(scheme):
     nx, nz, steps = 32, 16, 5
     got, ref = run_both(nx, nz, scheme, plume_start(nx, nz, seed=3), 2e-4, steps, Ra=1e5, dtype=torch.float32)

@@ -102,3 +102,46 @@ def test_buoyancy_lifts_the_hot_spot():
     z = (np.arange(nz) + 0.5) * box.dz
     ih, ic, kz = np.argmin(np.abs(x - 0.25)), np.argmin(np.abs(x - 0.5)), np.argmin(np.abs(z - 0.2))
     assert box.w[kz, ih] > 0 > box.w[kz, ic]
+
+
+def test_one_step_from_rest_scales_with_ra_pr():
+    """From U = 0 the first step has no advection and no viscous term, so the
+    new velocity is the projection of dt Ra Pr theta e_z: linear in Ra Pr
+    (eq. e:nsnd's buoyancy carries both factors), and theta does not depend on
+    them."""
+    nx, nz = 16, 8
+    th = W.rb_spots(nx, nz, hot=(0.5, 0.4), cold=(1.2, 0.5), r=0.2)
+    runs = {}
+    for Ra, Pr in ((1e4, 1.0), (1e4, 2.5), (2.5e4, 1.0)):
+        box = R.Box(nx, nz, Ra=Ra, Pr=Pr, scheme="CEC")
+        box.theta = th.copy()
+        box.step(1e-4)
+        runs[(Ra, Pr)] = (box.u, box.w, box.theta)
+    u1, w1, t1 = runs[(1e4, 1.0)]
+    assert np.abs(w1).max() > 0
+    for key in ((1e4, 2.5), (2.5e4, 1.0)):
+        u, w, t = runs[key]
+        assert np.allclose(u, 2.5 * u1, rtol=0, atol=1e-12 * np.abs(u).max())
+        assert np.allclose(w, 2.5 * w1, rtol=0, atol=1e-12 * np.abs(w).max())
+        assert np.array_equal(t, t1)
+
+
+def test_viscous_term_is_linear_in_pr():
+    """With Ra = 0 and theta = 0 one step from a velocity field differs from
+    the Pr = 0 step by Pr times the (projected) viscous increment dt lap U;
+    theta, which gains dt w from the base-state gradient (eq. e:Tnd), does not
+    depend on Pr."""
+    rng = np.random.default_rng(3)
+    nx, nz = 16, 8
+    u0, w0 = 0.3 * rng.standard_normal((nz, nx)), 0.3 * rng.standard_normal((nz, nx))
+    out = {}
+    for Pr in (0.0, 1.0, 0.7):
+        box = R.Box(nx, nz, Ra=0.0, Pr=Pr, scheme="FEC")
+        box.u, box.w = u0.copy(), w0.copy()
+        box.step(1e-4)
+        out[Pr] = (box.u, box.w, box.theta)
+    assert np.array_equal(out[0.7][2], out[0.0][2]) and np.abs(out[0.0][2]).max() > 0
+    for k in range(2):
+        inc = out[1.0][k] - out[0.0][k]
+        assert np.abs(inc).max() > 1e-6
+        assert np.allclose(out[0.7][k] - out[0.0][k], 0.7 * inc, rtol=0, atol=1e-12)
