@@ -212,3 +212,27 @@ def test_state_round_trip_and_argument_errors():
         sl.sl_rb_create(8, 8, Lx=0.0)
     with pytest.raises(sl.SLError):
         sl.sl_rb_create(8, 8, dtype=sl.F32_D64)
+
+
+@pytest.mark.parametrize("nx,nz,dt", [(4, 4, 1e-3), (4096, 48, 2e-8)])
+def test_smallest_and_largest_boxes_keep_the_mirror_symmetry(nx, nz, dt):
+    """The box's extreme sizes (4 cells per axis; 4096 cells along x, where the
+    transforms sum 4096 terms) against a property that holds at any size: a
+    start symmetric about x = Lx / 2 stays symmetric (theta, w even, u odd).
+    The bound allows the transforms' rounding, 1e-11 of the field's maximum."""
+    th = W.rb_spots(nx, nz, hot=(1.0, 0.3), cold=(1.0, 0.7), r=0.25)
+    th = 0.5 * (th + th[:, ::-1])
+    g = sl.RayleighBenard(nx, nz, Ra=1e5, scheme="CEC")
+    try:
+        z = torch.zeros((nz, nx), dtype=torch.float64)
+        g.set_state(z, z, torch.from_numpy(np.ascontiguousarray(th)))
+        sl.sl_device_status()
+        g.step(dt, 3)
+        u, w, th = (t.cpu().numpy() for t in g.state())
+        assert sl.sl_device_status() == 0
+    finally:
+        g.close()
+    assert np.isfinite(u).all() and np.isfinite(w).all() and np.isfinite(th).all()
+    assert np.abs(w).max() > 0
+    for f, s in ((th, 1), (w, 1), (u, -1)):
+        assert np.allclose(f, s * f[:, ::-1], rtol=0, atol=1e-11 * np.abs(f).max())
