@@ -349,6 +349,10 @@ def jsonl_records(line, when=None):
         recs.append(dict(base, record="learned_c4", gcell_s=lc["learned_gcell_s"],
                          roofline_frac=lc["roofline"]["frac"], fell_back_at_step=lc.get("fell_back_at_step"),
                          checks=lc.get("checks")))
+        if lc.get("deformation_c5_learned"):
+            dl = lc["deformation_c5_learned"]
+            recs.append(dict(base, record="deformation_c5_learned", fell_back_at_step=dl["fell_back_at_step"],
+                             rel_l2_vs_exact=dl["rel_l2_at_T"]))
     if line.get("rotation_c1"):
         r = line["rotation_c1"]
         recs.append(dict(base, record="rotation_c1", **{k: {"rel_l2_vs_exact": v["rel_l2"], "linf_vs_exact": v["linf"]}
@@ -696,6 +700,9 @@ def learned_measurement(torch, sl, stream, n=256, steps=500, check_every=25):
                     sl.sl_advect(y, x, vel, 3, dims, sp, d, sl.CEC, sl.F32, k & 1, stream)
                 x, y = y, x
             rt[name] = sl.sl_norms(x, phi, phi.numel(), sl.F32, stream)[2]
+        del a, b, x, y, phi, vel
+        torch.cuda.empty_cache()
+        deform = deformation_learned_run(torch, sl, stream, c)
     finally:
         sl.sl_corrector_destroy(c)
     peak, kind = measured_bf16_peak()
@@ -708,7 +715,46 @@ def learned_measurement(torch, sl, stream, n=256, steps=500, check_every=25):
                          "unit": "TFLOP/s", "frac": tflops / peak, "peak_kind": kind,
                          "flop_per_cell": LEARNED_TC_FLOP_PER_CELL},
             "steps": steps, "check_every": check_every, "fell_back_at_step": fell_at, "checks": checks[:6],
-            "roundtrip_rel_l2_100_100": rt}
+            "roundtrip_rel_l2_100_100": rt, "deformation_c5_learned": deform}
+
+
+def deformation_learned_run(torch, sl, stream, c, n=512, total_steps=2000, check_every=25):
+    """Config 5 in its learned form: the time-reversing deformation flow at
+    n^3, the three velocity components and the scalar each advanced by
+    sl_advect_learned (plain-scheme check every `check_every` steps, fallback
+    above 2x the plain error; one corrector, so a fallback holds for every
+    field), velocity scaled by cos(pi t / T) as in the plain and multi-field
+    runs; relative L2 error of each field at t = T against its initial field."""
+    from paper_1606_06117_gb300 import workloads as W
+    shape = (n, n, n)
+    vel = W.deformation_velocity(shape, device="cuda", dtype=torch.float32)
+    scal = W.random_modes(shape, W.draw_modes(3, 32, 8, seed=5), length=1.0, device="cuda", dtype=torch.float32)
+    f0 = [vel[0].clone(), vel[1].clone(), vel[2].clone(), scal]
+    sp = [1.0 / n] * 3
+    dt = 0.8 * sp[0] / float(vel.abs().amax())
+    T = total_steps * dt
+    sl.sl_corrector_reset(c)
+    cur = [f.clone() for f in f0]
+    nxt = [torch.empty_like(f) for f in f0]
+    fell_at, checks = None, []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(total_steps):
+        d = dt * math.cos(math.pi * (k + 0.5) * dt / T)
+        chk = int(k % check_every == 0)
+        for i in range(4):
+            used, errs = sl.sl_advect_learned(c, nxt[i], cur[i], vel, 3, [n] * 3, sp, d, k & 1, chk, 2.0, stream)
+            if chk and i == 3 and len(checks) < 4:
+                checks.append({"step": k, "learned_err": errs[0], "plain_err": errs[1], "plain_used": used})
+            if used and fell_at is None:
+                fell_at = k
+        cur, nxt = nxt, cur
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    errs = [sl.sl_norms(x, f, f.numel(), sl.F32, stream)[2] for x, f in zip(cur, f0)]
+    return {"grid": [n] * 3, "fields": 4, "steps_T": total_steps, "check_every": check_every,
+            "fell_back_at_step": fell_at, "checks": checks, "seconds": secs,
+            "rel_l2_at_T": {"u": errs[0], "v": errs[1], "w": errs[2], "scalar": errs[3]}}
 
 
 def rotation_measurement(torch, sl, stream, n=128):
