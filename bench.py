@@ -991,6 +991,13 @@ def deformation_measurement(torch, sl, stream, n=512, total_steps=2000, timed=20
         step(k)
     torch.cuda.synchronize()
     ms = time_steps(torch, stream, lambda k: step(2 + k), timed)
+
+    def plain(k):   # the same step as four single-field calls (bitwise the same result)
+        scale = math.cos(math.pi * (k + 0.5) * dt / T)
+        for i in range(4):
+            sl.sl_advect(nxt[i], cur[i], vel, 3, [n, n, n], sp, dt * scale, sl.CEC, sl.F32, k & 1, stream)
+        cur[:], nxt[:] = nxt[:], cur[:]
+    ms_plain = time_steps(torch, stream, lambda k: plain(2 + timed + k), timed)
     # accuracy: the full forward-and-back run from the initial fields
     cur[:] = [f.clone() for f in f0]
     for k in range(total_steps):
@@ -999,6 +1006,7 @@ def deformation_measurement(torch, sl, stream, n=512, total_steps=2000, timed=20
     errs = [sl.sl_norms(c, f, f.numel(), sl.F32, stream)[2] for c, f in zip(cur, f0)]
     return {"grid": [n, n, n], "fields": 4, "steps_T": total_steps,
             "field_gcell_s": 4 * n ** 3 / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+            "plain_field_gcell_s": 4 * n ** 3 / (ms_plain * 1e-3) / 1e9, "plain_ms_per_step": ms_plain,
             "rel_l2_at_T": {"u": errs[0], "v": errs[1], "w": errs[2], "scalar": errs[3]}}
 
 
