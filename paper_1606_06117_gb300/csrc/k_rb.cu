@@ -229,16 +229,14 @@ __global__ void k_rb_copy(const T *src, T *dst, int nx, int nz, bool to_padded)
 int blocks_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
 
 // Threads per CTA for the per-cell kernels: FP64 arithmetic is scarce per SM,
-// so small boxes spread over as many SMs as there are (152 on this part)
-// before CTAs grow.
-int cell_block(int64_t n)
+// so small boxes spread over as many SMs as the device has before CTAs grow.
+int cell_block(int64_t n, int sms)
 {
     int b = 32;
-    while (b < 256 && (n + b - 1) / b > 4 * 152) b *= 2;
+    while (b < 256 && (n + b - 1) / b > 4 * sms) b *= 2;
     return b;
 }
 int cell_grid(int64_t n, int b) { return (int)std::min<int64_t>((n + b - 1) / b, 4096); }
-
 
 }  // namespace
 }  // namespace sl
@@ -246,19 +244,19 @@ int cell_grid(int64_t n, int b) { return (int)std::min<int64_t>((n + b - 1) / b,
 using namespace sl;
 
 struct sl_rb {
-    int device = -1;
+    int device = -1, sms = 1;
     int nx = 0, nz = 0, scheme = SL_CEC, dtype = SL_F64;
     double Lx = 2.0, Lz = 1.0, Ra = 0.0, Pr = 1.0;
     int64_t step = 0;
     size_t esz = 8;
-    int64_t plane = 0;     // padded plane: (nx + 2G) (nz + 2G) elements
+    int64_t plane = 0;     // padded plane: rb_px(nx) (nz + 2G) elements
     int cur = 0;           // which of the two state buffers holds step n
     void *mem = nullptr;   // one device allocation
     // padded planes: two states (u, w, theta back to back, so that (u, w) is
     // the velocity argument of the advection), the advected fields, (u2, w2)
     void *S[2] = {nullptr, nullptr}, *A = nullptr, *W = nullptr;
-    // interior arrays: divergence / transform work, phi
-    void *d = nullptr, *t1 = nullptr, *phi = nullptr;
+    // interior arrays (nz x nx): the face divergence D, its transform F, phi
+    void *d = nullptr, *F = nullptr, *phi = nullptr;
     // orthonormal DCT-II matrices C_x (and its transpose), C_z; eigenvalues per axis
     void *cx = nullptr, *cxT = nullptr, *cz = nullptr, *lx = nullptr, *lz = nullptr;
     int *signs = nullptr;   // sx of (u, w, theta), then sz of (u, w, theta)
@@ -279,14 +277,14 @@ int rb_step_t(sl_rb *r, double dt, int nsteps, cudaStream_t st)
     const int px = rb_px(nx), pz = nz + 2 * RBG;
     const int64_t P = r->plane;
     T *A = static_cast<T *>(r->A), *Wk = static_cast<T *>(r->W);
-    T *d = static_cast<T *>(r->d), *F = static_cast<T *>(r->t1), *phi = static_cast<T *>(r->phi);
+    T *d = static_cast<T *>(r->d), *F = static_cast<T *>(r->F), *phi = static_cast<T *>(r->phi);
     const T *cx = static_cast<const T *>(r->cx), *cxT = static_cast<const T *>(r->cxT);
     const T *cz = static_cast<const T *>(r->cz);
     const T *lx = static_cast<const T *>(r->lx), *lz = static_cast<const T *>(r->lz);
     const double dx = r->Lx / nx, dz = r->Lz / nz;
     const int64_t pdims[3] = {px, pz, 1};
     const double sp[3] = {dx, dz, 1.0};
-    const int cbk = cell_block(n), cgr = cell_grid(n, cbk);
+    const int cbk = cell_block(n, r->sms), cgr = cell_grid(n, cbk);
     const size_t rsm = sizeof(T) * (kRbRowThreads + nx);
     for (int s = 0; s < nsteps; ++s) {
         // S0 holds step n with its ghost layers (the walls' mirror images)
@@ -407,6 +405,7 @@ int sl_rb_create(sl_rb **out, int nx, int nz, double Lx, double Lz, double Ra, d
     sl_rb *r = new (std::nothrow) sl_rb();
     if (!r) return set_error(SL_ERR_NOMEM, "host allocation");
     r->device = c->device;
+    r->sms = c->num_sms > 0 ? c->num_sms : 1;
     r->nx = nx;
     r->nz = nz;
     r->Lx = Lx;
@@ -438,7 +437,7 @@ int sl_rb_create(sl_rb **out, int nx, int nz, double Lx, double Lz, double Ra, d
     r->A = take(3 * r->plane);
     r->W = take(3 * r->plane);
     r->d = take(n);
-    r->t1 = take(n);
+    r->F = take(n);
     r->phi = take(n);
     r->cx = take((int64_t)nx * nx);
     r->cxT = take((int64_t)nx * nx);
