@@ -190,6 +190,73 @@ k_rb_inverse(const T *F, const T *cz, const T *cx, T *phi, int nx, int nz)
     rb_vecmat(R, 1, cx, nx, nx, nx, part, [&](int i, T v) { pm[i] = v; });
 }
 
+// Copies n elements from global to shared memory: 16-byte chunks by cp.async
+// (both bases 16-byte aligned), the tail by plain loads.
+template <typename T>
+__device__ __forceinline__ void rb_stage(T *dst, const T *src, int64_t n)
+{
+    constexpr int V = 16 / sizeof(T);
+    const int64_t nv = n / V;
+    for (int64_t c = threadIdx.x; c < nv; c += blockDim.x) cp_async16(dst + c * V, src + c * V);
+    for (int64_t i = nv * V + threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// Elements a staged operand block takes, rounded up to a 16-byte multiple.
+template <typename T>
+__host__ __device__ constexpr int64_t rb_pad(int64_t n)
+{
+    return (n + 16 / (int64_t)sizeof(T) - 1) / (16 / (int64_t)sizeof(T)) * (16 / (int64_t)sizeof(T));
+}
+
+// The same transforms with their matrix operands staged in shared memory
+// first (small boxes: D or F and C_x^T or C_x fit), so that the sums read
+// shared memory instead of waiting on L2; same summation order, same results.
+template <typename T>
+__global__ void __launch_bounds__(kRbRowThreads)
+k_rb_forward_s(const T *D, const T *cz, const T *cxT, const T *lx, const T *lz, T *F, int nx, int nz)
+{
+    extern __shared__ __align__(16) unsigned char rb_smem[];
+    T *part = reinterpret_cast<T *>(rb_smem), *R = part + kRbRowThreads;
+    T *sD = R + rb_pad<T>(nx), *sC = sD + rb_pad<T>((int64_t)nz * nx);
+    rb_stage(sD, D, (int64_t)nz * nx);
+    rb_stage(sC, cxT, (int64_t)nx * nx);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    const int k = blockIdx.x;
+    rb_vecmat(cz + (int64_t)k * nz, 1, sD, nx, nz, nx, part, [&](int i, T v) { R[i] = v; });
+    T *Fk = F + (int64_t)k * nx;
+    const T lk = lz[k];
+    rb_vecmat(R, 1, sC, nx, nx, nx, part,
+              [&](int j, T v) { Fk[j] = (k == 0 && j == 0) ? T(0) : v / (lk + lx[j]); });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRbRowThreads)
+k_rb_inverse_s(const T *F, const T *cz, const T *cx, T *phi, int nx, int nz)
+{
+    extern __shared__ __align__(16) unsigned char rb_smem[];
+    T *part = reinterpret_cast<T *>(rb_smem), *R = part + kRbRowThreads;
+    T *sF = R + rb_pad<T>(nx), *sC = sF + rb_pad<T>((int64_t)nz * nx);
+    rb_stage(sF, F, (int64_t)nz * nx);
+    rb_stage(sC, cx, (int64_t)nx * nx);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    const int m = blockIdx.x;
+    rb_vecmat(cz + m, nz, sF, nx, nz, nx, part, [&](int j, T v) { R[j] = v; });
+    T *pm = phi + (int64_t)m * nx;
+    rb_vecmat(R, 1, sC, nx, nx, nx, part, [&](int i, T v) { pm[i] = v; });
+}
+
+// Shared memory of the staged transforms, and the largest the box uses them for.
+template <typename T>
+size_t rb_staged_smem(int nx, int nz)
+{
+    return sizeof(T) * (size_t)(kRbRowThreads + rb_pad<T>(nx) + rb_pad<T>((int64_t)nz * nx) + (int64_t)nx * nx);
+}
+constexpr size_t kRbStagedMax = 96 * 1024;
+
 // Projection: cells take the average of their two faces' gradient corrections
 // (face gradient (phi_{i+1} - phi_i) / dx inside, zero on the walls); the
 // result is the new u, w with their ghost images.
@@ -245,6 +312,7 @@ using namespace sl;
 
 struct sl_rb {
     int device = -1, sms = 1;
+    bool staged = false;   // transforms with staged operands (small boxes)
     int nx = 0, nz = 0, scheme = SL_CEC, dtype = SL_F64;
     double Lx = 2.0, Lz = 1.0, Ra = 0.0, Pr = 1.0;
     int64_t step = 0;
@@ -285,7 +353,7 @@ int rb_step_t(sl_rb *r, double dt, int nsteps, cudaStream_t st)
     const int64_t pdims[3] = {px, pz, 1};
     const double sp[3] = {dx, dz, 1.0};
     const int cbk = cell_block(n, r->sms), cgr = cell_grid(n, cbk);
-    const size_t rsm = sizeof(T) * (kRbRowThreads + nx);
+    const size_t rsm = sizeof(T) * (kRbRowThreads + nx), ssm = rb_staged_smem<T>(nx, nz);
     for (int s = 0; s < nsteps; ++s) {
         // S0 holds step n with its ghost layers (the walls' mirror images)
         T *S0 = static_cast<T *>(r->S[r->cur]), *S1 = static_cast<T *>(r->S[r->cur ^ 1]);
@@ -301,8 +369,13 @@ int rb_step_t(sl_rb *r, double dt, int nsteps, cudaStream_t st)
                                             nz, T(dt), T(r->Ra), T(r->Pr), T(1.0 / (dx * dx)), T(1.0 / (dz * dz)),
                                             T(1.0 / dx), T(1.0 / dz));
         // phi = C_z^T [(C_z D C_x^T) / lam] C_x
-        k_rb_forward<T><<<nz, kRbRowThreads, rsm, st>>>(d, cz, cxT, lx, lz, F, nx, nz);
-        k_rb_inverse<T><<<nz, kRbRowThreads, rsm, st>>>(F, cz, cx, phi, nx, nz);
+        if (r->staged) {
+            k_rb_forward_s<T><<<nz, kRbRowThreads, ssm, st>>>(d, cz, cxT, lx, lz, F, nx, nz);
+            k_rb_inverse_s<T><<<nz, kRbRowThreads, ssm, st>>>(F, cz, cx, phi, nx, nz);
+        } else {
+            k_rb_forward<T><<<nz, kRbRowThreads, rsm, st>>>(d, cz, cxT, lx, lz, F, nx, nz);
+            k_rb_inverse<T><<<nz, kRbRowThreads, rsm, st>>>(F, cz, cx, phi, nx, nz);
+        }
         // the projected u, w (with ghosts) of the next state
         k_rb_project<T><<<cgr, cbk, 0, st>>>(Wk, Wk + P, phi, S1, S1 + P, nx, nz, T(1.0 / dx), T(1.0 / dz));
         const cudaError_t e = cudaGetLastError();
@@ -470,6 +543,20 @@ int sl_rb_create(sl_rb **out, int nx, int nz, double Lx, double Lz, double Ra, d
     up(r->lx, lxv);
     up(r->lz, lzv);
     if (e == cudaSuccess) e = cudaMemcpy(r->signs, signs, sizeof signs, cudaMemcpyHostToDevice);
+    // small boxes stage the transforms' matrix operands in shared memory
+    const size_t ssm = dtype == SL_F64 ? rb_staged_smem<double>(nx, nz) : rb_staged_smem<float>(nx, nz);
+    if (e == cudaSuccess && ssm <= kRbStagedMax) {
+        if (dtype == SL_F64) {
+            e = cudaFuncSetAttribute(k_rb_forward_s<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_rb_inverse_s<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+        } else {
+            e = cudaFuncSetAttribute(k_rb_forward_s<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_rb_inverse_s<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+        }
+        r->staged = e == cudaSuccess;
+    }
     if (e != cudaSuccess) {
         cudaFree(r->mem);
         delete r;
