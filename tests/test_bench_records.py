@@ -38,3 +38,22 @@ def test_records_cover_every_measurement(tmp_path):
     lines = p.read_text().splitlines()
     assert len(lines) == 2 * len(recs)
     assert all(json.loads(x)["record"] for x in lines)
+
+
+def test_records_of_the_learned_and_rayleigh_benard_measurements():
+    line = dict(LINE)
+    line["learned_c4"] = {"learned_gcell_s": 20.3, "roofline": {"frac": 0.18}, "fell_back_at_step": 125,
+                          "checks": [{"step": 0}],
+                          "deformation_c5_learned": {"fell_back_at_step": 0, "rel_l2_at_T": {"u": 3.6e-4}}}
+    line["rayleigh_benard_f4"] = {"grid": [50, 50], "device_status": 0,
+                                  "CIR": {"us_per_step": 21.5, "top_reached_at_step": 990},
+                                  "CEC": {"us_per_step": 29.4, "top_reached_at_step": 970},
+                                  "cpu_baseline": {"value": 857.0}}
+    recs = bench.jsonl_records(line, when="t")
+    kinds = [r["record"] for r in recs]
+    i = kinds.index("learned_c4")
+    assert kinds[i + 1] == "deformation_c5_learned" and kinds[-1] == "rayleigh_benard_f4"
+    assert recs[i + 1]["fell_back_at_step"] == 0 and recs[i + 1]["rel_l2_vs_exact"] == {"u": 3.6e-4}
+    rb = recs[-1]
+    assert rb["grid"] == [50, 50] and rb["CEC"] == {"us_per_step": 29.4, "top_reached_at_step": 970}
+    assert "cpu_baseline" not in rb and "device_status" not in rb
