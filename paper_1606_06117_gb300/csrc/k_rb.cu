@@ -543,17 +543,20 @@ int sl_rb_create(sl_rb **out, int nx, int nz, double Lx, double Lz, double Ra, d
     up(r->lx, lxv);
     up(r->lz, lzv);
     if (e == cudaSuccess) e = cudaMemcpy(r->signs, signs, sizeof signs, cudaMemcpyHostToDevice);
-    // small boxes stage the transforms' matrix operands in shared memory
+    // small boxes stage the transforms' matrix operands in shared memory; the
+    // kernels' limit is per function, not per box, so it is raised to the cap
+    // that every staged box fits under
     const size_t ssm = dtype == SL_F64 ? rb_staged_smem<double>(nx, nz) : rb_staged_smem<float>(nx, nz);
     if (e == cudaSuccess && ssm <= kRbStagedMax) {
+        const int cap = (int)kRbStagedMax;
         if (dtype == SL_F64) {
-            e = cudaFuncSetAttribute(k_rb_forward_s<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+            e = cudaFuncSetAttribute(k_rb_forward_s<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
             if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_rb_inverse_s<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+                e = cudaFuncSetAttribute(k_rb_inverse_s<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
         } else {
-            e = cudaFuncSetAttribute(k_rb_forward_s<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+            e = cudaFuncSetAttribute(k_rb_forward_s<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
             if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_rb_inverse_s<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+                e = cudaFuncSetAttribute(k_rb_inverse_s<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
         }
         r->staged = e == cudaSuccess;
     }

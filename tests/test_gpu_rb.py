@@ -238,3 +238,36 @@ def test_smallest_and_largest_boxes_keep_the_mirror_symmetry(nx, nz, dt):
     assert np.abs(w).max() > 0
     for f, s in ((th, 1), (w, 1), (u, -1)):
         assert np.allclose(f, s * f[:, ::-1], rtol=0, atol=1e-11 * np.abs(f).max())
+
+
+def test_boxes_of_different_sizes_step_side_by_side():
+    """Two live boxes whose transforms stage different amounts of shared memory
+    (80 x 40: 79.5 KB, 24 x 12: 9 KB), created large first, stepped in turn:
+    each gives the result it gives alone."""
+    def start(nx, nz):
+        u, w, th = plume_start(nx, nz, seed=nx)
+        return [torch.from_numpy(np.ascontiguousarray(a)) for a in (u, w, th)]
+    solo = {}
+    for nx, nz in ((80, 40), (24, 12)):
+        g = sl.RayleighBenard(nx, nz, Ra=1e5, scheme="CEC")
+        try:
+            g.set_state(*start(nx, nz))
+            g.step(2e-5, 20)
+            solo[nx] = g.state()
+        finally:
+            g.close()
+    a = sl.RayleighBenard(80, 40, Ra=1e5, scheme="CEC")
+    b = sl.RayleighBenard(24, 12, Ra=1e5, scheme="CEC")
+    try:
+        a.set_state(*start(80, 40))
+        b.set_state(*start(24, 12))
+        for _ in range(4):
+            b.step(2e-5, 5)
+            a.step(2e-5, 5)
+        for x, y in zip(a.state(), solo[80]):
+            assert torch.equal(x, y)
+        for x, y in zip(b.state(), solo[24]):
+            assert torch.equal(x, y)
+    finally:
+        a.close()
+        b.close()
