@@ -1,7 +1,7 @@
 """Convergence orders and the paper's qualitative rankings, on the FP64 oracle.
 
-The spec claim is order 1 / 2 / 2 / 3 for CIR / FEC / BEC / CEC on a
-smooth Gaussian under refinement; translations at a constant non-aligned
+The schemes converge with orders 1 / 2 / 2 / 3 (CIR / FEC / BEC / CEC, Sec. 3
+and Table 1) on a smooth Gaussian under refinement; translations at a constant non-aligned
 velocity have exact trajectories, so the error is the scheme's own.
 """
 import math
