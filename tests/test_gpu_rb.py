@@ -271,3 +271,34 @@ def test_boxes_of_different_sizes_step_side_by_side():
     finally:
         a.close()
         b.close()
+
+
+def test_steps_on_a_side_stream_equal_steps_on_the_default_stream():
+    """sl_rb_step enqueues on the caller's stream (eager kernels and replayed
+    graphs alike); a box stepped on a side stream ends where the same box
+    stepped on the default stream does."""
+    nx, nz = 24, 12
+    u, w, th = plume_start(nx, nz, seed=9)
+    start = [torch.from_numpy(np.ascontiguousarray(a)) for a in (u, w, th)]
+    res = []
+    for use_side in (False, True):
+        g = sl.RayleighBenard(nx, nz, Ra=1e5, scheme="CEC")
+        try:
+            g.set_state(*start)
+            if use_side:
+                s = torch.cuda.Stream()
+                with torch.cuda.stream(s):
+                    g.step(2e-5, 3)
+                    g.step(2e-5, 24)
+                    out = g.state()
+                s.synchronize()
+            else:
+                g.step(2e-5, 3)
+                g.step(2e-5, 24)
+                out = g.state()
+                torch.cuda.synchronize()
+            res.append([t.clone() for t in out])
+        finally:
+            g.close()
+    for x, y in zip(*res):
+        assert torch.equal(x, y)
